@@ -1,0 +1,243 @@
+"""CPU oracle for the clover Wilson operator and its BiCGStab solvers.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
+CPU-baseline leg of the benchmark, never by the product package.  The
+arithmetic lives in plain C (qcd_oracle.c, FP64, written from the paper's
+definitions); this module only compiles it with gcc and marshals numpy
+arrays through ctypes.  See qcd_oracle.c for the definitions followed and the
+passages of the paper they come from.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qcd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(
+            ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _lib.oracle_true_residual.restype = ctypes.c_double
+    return _lib
+
+
+def _dims(dims):
+    return (ctypes.c_int * 4)(*[int(d) for d in dims])
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def volume(dims) -> int:
+    return int(np.prod([int(d) for d in dims]))
+
+
+# ---------------------------------------------------------------- algebra
+def gamma(which: int) -> np.ndarray:
+    """gamma_mu for which = 0..3 (x, y, z, t) and gamma5 for which = 4."""
+    out = np.zeros((4, 4), dtype=np.complex128)
+    lib().oracle_gamma(ctypes.c_int(which), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- operator
+def hopping(dims, t_bc, U, psi, dagger=False):
+    """H psi on the full lattice (Eq. 4); dagger gives gamma5 H gamma5."""
+    U, psi = _c(U), _c(psi)
+    out = np.empty_like(psi)
+    lib().oracle_hopping(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(psi), _p(out), ctypes.c_int(int(dagger)))
+    return out
+
+
+def clover_field(dims, U, kappa, csw):
+    """F(n) as [V, 12, 12], index 3*spin + colour."""
+    U = _c(U)
+    F = np.empty((volume(dims), 12, 12), dtype=np.complex128)
+    lib().oracle_clover_field(_dims(dims), _p(U), ctypes.c_double(kappa), ctypes.c_double(csw), _p(F))
+    return F
+
+
+def field_strength(dims, U, site, mu, nu):
+    """F_munu(n) = (Q - Q^dag)/(8i) at one site, [3, 3]."""
+    U = _c(U)
+    out = np.empty((3, 3), dtype=np.complex128)
+    lib().oracle_field_strength(_dims(dims), _p(U), ctypes.c_long(site), ctypes.c_int(mu), ctypes.c_int(nu), _p(out))
+    return out
+
+
+def invert_sites(F):
+    F = _c(F)
+    Fi = np.empty_like(F)
+    rc = lib().oracle_invert_sites(ctypes.c_long(F.shape[0]), _p(F), _p(Fi))
+    if rc != 0:
+        raise ArithmeticError("singular clover block")
+    return Fi
+
+
+def site_apply(M, psi):
+    M, psi = _c(M), _c(psi)
+    out = np.empty_like(psi)
+    lib().oracle_site_apply(ctypes.c_long(M.shape[0]), _p(M), _p(psi), _p(out))
+    return out
+
+
+def dirac(dims, t_bc, U, F, kappa, psi):
+    """D psi = F psi - kappa H psi (Eq. 3)."""
+    U, F, psi = _c(U), _c(F), _c(psi)
+    out = np.empty_like(psi)
+    lib().oracle_dirac(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(F), ctypes.c_double(kappa), _p(psi), _p(out))
+    return out
+
+
+def dirac_sites(dims, t_bc, U, kappa, csw, psi, sites):
+    """(D psi)(n) at the listed sites only, [len(sites), 4, 3]."""
+    U, psi = _c(U), _c(psi)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+    lib().oracle_dirac_sites(_dims(dims), ctypes.c_int(t_bc), _p(U), ctypes.c_double(kappa), ctypes.c_double(csw),
+                             _p(psi), ctypes.c_long(len(sites)), _p(sites), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- even-odd
+def half_to_full(dims, parity, half):
+    half = _c(half)
+    full = np.empty((volume(dims), 4, 3), dtype=np.complex128)
+    lib().oracle_half_to_full(_dims(dims), ctypes.c_int(parity), _p(half), _p(full))
+    return full
+
+
+def full_to_half(dims, parity, full):
+    full = _c(full)
+    half = np.empty((volume(dims) // 2, 4, 3), dtype=np.complex128)
+    lib().oracle_full_to_half(_dims(dims), ctypes.c_int(parity), _p(full), _p(half))
+    return half
+
+
+def field_to_half(dims, parity, F):
+    F = _c(F)
+    out = np.empty((volume(dims) // 2, 12, 12), dtype=np.complex128)
+    lib().oracle_field_to_half(_dims(dims), ctypes.c_int(parity), _p(F), _p(out))
+    return out
+
+
+def hop_eo(dims, t_bc, U, out_parity, in_half, dagger=False):
+    """H_{p,1-p} on half-lattice vectors."""
+    U, in_half = _c(U), _c(in_half)
+    out = np.empty_like(in_half)
+    lib().oracle_hop_eo(_dims(dims), ctypes.c_int(t_bc), _p(U), ctypes.c_int(out_parity), _p(in_half), _p(out),
+                        ctypes.c_int(int(dagger)))
+    return out
+
+
+def mult(dims, t_bc, U, Finv, out_parity, in_half):
+    """MULT = F_pp^-1 H_{p,1-p} (Sec. II-B); Finv is the full [V,12,12] field."""
+    U, Finv, in_half = _c(U), _c(Finv), _c(in_half)
+    out = np.empty_like(in_half)
+    lib().oracle_mult(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(Finv), ctypes.c_int(out_parity), _p(in_half), _p(out))
+    return out
+
+
+def dhat(dims, t_bc, U, Finv, kappa, p):
+    """D^_ee p = p - kappa^2 H~_eo H~_oe p (Eq. 8)."""
+    U, Finv, p = _c(U), _c(Finv), _c(p)
+    q = np.empty_like(p)
+    lib().oracle_dhat(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(Finv), ctypes.c_double(kappa), _p(p), _p(q))
+    return q
+
+
+def eo_source(dims, t_bc, U, Finv, kappa, b):
+    """b^_e = F_ee^-1 b_e + kappa H~_eo F_oo^-1 b_o (Eq. 6)."""
+    U, Finv, b = _c(U), _c(Finv), _c(b)
+    out = np.empty((volume(dims) // 2, 4, 3), dtype=np.complex128)
+    lib().oracle_eo_source(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(Finv), ctypes.c_double(kappa), _p(b), _p(out))
+    return out
+
+
+def eo_reconstruct(dims, t_bc, U, Finv, kappa, b, x_e):
+    """Full solution from x_e with x_o = F_oo^-1 b_o + kappa H~_oe x_e (Eq. 7)."""
+    U, Finv, b, x_e = _c(U), _c(Finv), _c(b), _c(x_e)
+    x = np.empty((volume(dims), 4, 3), dtype=np.complex128)
+    lib().oracle_eo_reconstruct(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(Finv), ctypes.c_double(kappa), _p(b),
+                                _p(x_e), _p(x))
+    return x
+
+
+def true_residual(dims, t_bc, U, F, kappa, b, x) -> float:
+    """||b - D x|| / ||b|| on the full lattice."""
+    U, F, b, x = _c(U), _c(F), _c(b), _c(x)
+    return float(lib().oracle_true_residual(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(F), ctypes.c_double(kappa),
+                                            _p(b), _p(x)))
+
+
+# ---------------------------------------------------------------- solvers
+def bicgstab_full(dims, t_bc, U, F, kappa, b, tol, maxit=10000):
+    """Unpreconditioned BiCGStab on D from x = 0; returns (x, status, iters)."""
+    U, F, b = _c(U), _c(F), _c(b)
+    x = np.empty_like(b)
+    it = ctypes.c_int(0)
+    st = lib().oracle_bicgstab_full(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(F), ctypes.c_double(kappa), _p(b),
+                                    _p(x), ctypes.c_double(tol), ctypes.c_int(maxit), ctypes.byref(it))
+    return x, st, it.value
+
+
+def bicgstab_eo(dims, t_bc, U, Finv, kappa, b, tol_eo, maxit=10000):
+    """Even-odd preconditioned BiCGStab on D^_ee; returns (x_full, status, iters)."""
+    U, Finv, b = _c(U), _c(Finv), _c(b)
+    x = np.empty_like(b)
+    it = ctypes.c_int(0)
+    st = lib().oracle_bicgstab_eo(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(Finv), ctypes.c_double(kappa), _p(b),
+                                  _p(x), ctypes.c_double(tol_eo), ctypes.c_int(maxit), ctypes.byref(it))
+    return x, st, it.value
+
+
+def nested_bicgstab(dims, t_bc, U, Finv, kappa, b, tol_eo, inner_tol, inner_maxit=250, maxit=100):
+    """Alg. 1 with Alg. 2 as the inner solve, all in FP64; returns
+    (x_full, status, outer_iterations, inner_applications)."""
+    U, Finv, b = _c(U), _c(Finv), _c(b)
+    x = np.empty_like(b)
+    outer = ctypes.c_int(0)
+    inner = ctypes.c_int(0)
+    st = lib().oracle_nested_bicgstab(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(Finv), ctypes.c_double(kappa), _p(b),
+                                      _p(x), ctypes.c_double(tol_eo), ctypes.c_double(inner_tol),
+                                      ctypes.c_int(inner_maxit), ctypes.c_int(maxit), ctypes.byref(outer),
+                                      ctypes.byref(inner))
+    return x, st, outer.value, inner.value
+
+
+# ---------------------------------------------------------------- gradient
+def link_grad(dims, t_bc, U, kappa, csw, x, lam):
+    """Gradient of f(U) = -Re<lam, D[U] x> with x, lam fixed, in the
+    convention G = df/dRe U + i df/dIm U; [V, 4, 3, 3]."""
+    U, x, lam = _c(U), _c(x), _c(lam)
+    G = np.empty_like(U)
+    lib().oracle_link_grad(_dims(dims), ctypes.c_int(t_bc), _p(U), ctypes.c_double(kappa), ctypes.c_double(csw),
+                           _p(x), _p(lam), _p(G))
+    return G
