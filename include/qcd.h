@@ -1,0 +1,213 @@
+/*
+ * qcd.h -- C ABI of the GB300 (sm_103a) library for the even-odd
+ * preconditioned O(a)-improved (clover) Wilson operator and the nested
+ * mixed-precision BiCGStab that solves with it.
+ *
+ * The paper this follows: Boku, Ishikawa, Kuramashi, Meadows, "Mixed
+ * Precision Solver Scalable to 16000 MPI Processes for Lattice QCD
+ * Simulations on the Oakforest-PACS System" (arXiv:1709.08785).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * Lattice: extents dims = {Lx, Ly, Lz, Lt}, every extent even and >= 2;
+ *   site n = (x, y, z, t), lexicographic index s = x + Lx*(y + Ly*(z + Lz*t));
+ *   parity (x+y+z+t) mod 2, 0 = even ("e"), 1 = odd ("o") (Sec. II-B).
+ *   A half-lattice vector of parity p holds the sites of that parity in the
+ *   order of cb = s/2.
+ * Fields handed across the boundary (all canonical, row-major, interleaved
+ *   complex, i.e. C99 double _Complex / float _Complex):
+ *   gauge    U[s][mu][i][j], mu = x, y, z, t, U_mu(n) the link n -> n+mu,
+ *            complex128, SU(3) (det U = 1 is assumed by the 12-real storage)
+ *   spinor   psi[s][alpha][i], spin alpha = 0..3, colour i = 0..2
+ *   half     psi[cb][alpha][i] on one parity
+ * Gamma matrices: Dirac basis, gamma_k = [[0, -i s_k], [i s_k, 0]] (k = x,
+ *   y, z), gamma_t = diag(1, 1, -1, -1) (gamma_t diagonal, Sec. II-A),
+ *   gamma5 = gamma_x gamma_y gamma_z gamma_t = -[[0, 1], [1, 0]].
+ * Operator (Sec. II-A, Eqs. 3-4):
+ *   D = F - kappa H,
+ *   H(n,m) = sum_mu (1 - gamma_mu) U_mu(n) delta_{n+mu,m}
+ *                 + (1 + gamma_mu) U_mu(m)^dag delta_{n-mu,m},
+ *   F(n) = 1 - (csw kappa / 2) sum_{mu != nu} sigma_munu F_munu(n),
+ *   sigma_munu = (i/2)[gamma_mu, gamma_nu], F_munu = (Q_munu - Q_munu^dag)/(8i),
+ *   Q_munu the sum of the four plaquette leaves around n (the clover term
+ *   the paper cites; stored as two 6x6 Hermitian blocks, Sec. III-A).
+ *   t_bc = -1 multiplies the hops that cross the time boundary by -1
+ *   (antiperiodic quark fields); the clover term uses the unmodified links.
+ *
+ * Precisions: QCD_F64 operates on complex128 buffers; QCD_F32 on complex64
+ *   buffers; QCD_F16 on complex64 buffers that are stored internally in IEEE
+ *   half with one float scale per site (links and clover in half too) and
+ *   operated on in FP32.
+ *
+ * Memory and streams: pointers marked "device" must be device memory of the
+ *   context's device; all work is ordered on the context's stream; calls
+ *   return when the work is enqueued unless stated otherwise.  The caller
+ *   owns every buffer it passes; the context owns the gauge and clover
+ *   fields and its workspaces.  A context is not thread-safe.
+ * Errors: every call returns a qcd_status; on failure the output buffers
+ *   are unspecified, the context stays usable, and qcd_last_error() gives a
+ *   message for the calling thread.
+ */
+#ifndef QCD_GB300_H
+#define QCD_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qcd_ctx qcd_ctx;
+
+typedef enum {
+    QCD_OK = 0,
+    QCD_EINVAL = -1,            /* bad argument (null pointer, size, flag) */
+    QCD_ECUDA = -2,             /* a CUDA runtime call failed */
+    QCD_ENOMEM = -3,            /* device or host allocation failed */
+    QCD_ENOTCONV = -4,          /* iteration cap reached before the tolerance */
+    QCD_EBREAKDOWN = -5,        /* BiCGStab breakdown (rho or omega zero or non-finite) */
+    QCD_ENONFINITE = -6,        /* non-finite input or intermediate */
+    QCD_ECLOVER_SINGULAR = -7,  /* a clover block has a zero pivot */
+    QCD_ETIMEOUT = -8,          /* a bounded device wait gave up */
+    QCD_ESTATE = -9             /* call out of order (e.g. no gauge field loaded) */
+} qcd_status;
+
+typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2 } qcd_prec;
+
+/* Create a context for one lattice on the current CUDA device.
+ * dims: host array of 4 even extents >= 2 (Lx*Ly*Lz*Lt < 2^31).
+ * t_bc: +1 periodic or -1 antiperiodic in time (Sec. II-A states periodic
+ *       boundaries; antiperiodic time is the usual choice for quarks).
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: QCD_EINVAL for bad dims or t_bc. */
+int qcd_create(qcd_ctx **ctx, const int dims[4], int t_bc, void *stream);
+int qcd_destroy(qcd_ctx *ctx);
+/* change the stream later calls are ordered on */
+int qcd_set_stream(qcd_ctx *ctx, void *stream);
+
+/* Load the gauge field U (canonical complex128 [V][4][3][3]), from device
+ * memory (on_device = 1) or host memory (0), and build the internal copies:
+ * FP64 with 18 reals per link, FP32 and FP16 with the first two columns
+ * only (12 reals, SU(3) reconstruction, Sec. III-A) -- the conversion
+ * [U, F] -> [U^SP, F^SP] of Alg. 1.  Invalidates the clover term.
+ * Synchronous with respect to the host buffer (it may be reused on return). */
+int qcd_gauge_load(qcd_ctx *ctx, const void *U, int on_device);
+
+/* Build the clover term F and its site-local inverse F^-1 (Sec. II-B: F_ee,
+ * F_oo are block diagonal and "inverted easily") in FP64 from the FP64
+ * links, as two 6x6 Hermitian blocks per site in the chiral basis
+ * (Sec. III-A), then round them to FP32 and FP16.
+ * Errors: QCD_ESTATE without a gauge field; QCD_ECLOVER_SINGULAR if a block
+ * has a (near-)zero pivot. */
+int qcd_clover_build(qcd_ctx *ctx, double kappa, double csw);
+
+/* out = H_{p,1-p} in (Eq. 4 restricted to one parity, Sec. II-B), or with
+ * dagger = 1, gamma5 H gamma5 = H^dag.  out has parity out_parity, in the
+ * opposite parity.  in/out: device half vectors, complex128 for QCD_F64 and
+ * complex64 otherwise, nrhs of them back to back ([nrhs][Vh][4][3]).
+ * The right-hand sides share every link load. */
+int qcd_dslash_eo(qcd_ctx *ctx, void *out, const void *in, int out_parity, int dagger, int prec, int nrhs);
+
+/* out = F_pp in (inverse = 0) or F_pp^-1 in (inverse = 1) on parity p.
+ * Same buffer conventions as qcd_dslash_eo.  Needs qcd_clover_build. */
+int qcd_clover_apply(qcd_ctx *ctx, void *out, const void *in, int parity, int inverse, int prec, int nrhs);
+
+/* MULT (Sec. II-B): out = F_pp^-1 H_{p,1-p} in, the fused hopping + clover
+ * inverse kernel the paper optimises (H~_eo, H~_oe); with dagger = 1 the
+ * hopping term is gamma5 H gamma5.  Same buffer conventions. */
+int qcd_mult_eo(qcd_ctx *ctx, void *out, const void *in, int out_parity, int dagger, int prec, int nrhs);
+
+/* out = D^_ee in = in - kappa^2 H~_eo H~_oe in (Eq. 8; the printed
+ * "H~_eo H~_eo" read as the Schur complement's H~_eo H~_oe), on even half
+ * vectors.  Same buffer conventions (nrhs right-hand sides). */
+int qcd_dhat(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
+
+/* out = D in = F in - kappa H in on the full lattice (Eq. 3), FP64,
+ * canonical complex128 [V][4][3] device buffers. */
+int qcd_dirac(qcd_ctx *ctx, void *out, const void *in);
+
+typedef struct {
+    int precision_levels; /* 1: FP64 BiCGStab; 2: FP64 outer (Alg. 1) with
+                             FP32 inner (Alg. 2); 3: FP64 outer, FP32
+                             flexible middle, FP16-storage inner */
+    int even_odd;         /* 1: solve D^_ee x_e = b^_e (Eqs. 5-7); 0: plain
+                             BiCGStab on the full D (precision_levels 1 only) */
+    double inner_tol[2];  /* |r| exit threshold of the inner levels on their
+                             unit-norm right-hand side (Alg. 2); level 2, 3 */
+    int max_outer;        /* iteration cap of the FP64 level */
+    int max_inner[2];     /* iteration caps of the lower levels */
+    int max_restarts;     /* restarts from the true residual (FP64) */
+    int use_x0;           /* 1: x holds an initial guess; 0: x = 0 (Alg. 1) */
+} qcd_solve_opts;
+
+typedef struct {
+    int status;            /* qcd_status of the solve */
+    int outer_iters;       /* FP64-level iterations */
+    int inner_iters[2];    /* iterations summed over the lower levels */
+    int restarts;          /* true-residual restarts */
+    long dhat_applies[3];  /* D^ (or D) applications by precision F64/F32/F16 */
+    double true_resid;     /* ||b - D x|| / ||b|| in FP64 at exit */
+    double seconds;        /* wall time of the call (device events) */
+} qcd_solve_info;
+
+/* Defaults: precision_levels 2, even_odd 1, inner_tol {1e-5, 1e-2},
+ * max_outer 200, max_inner {250, 250}, max_restarts 5, use_x0 0. */
+void qcd_solve_opts_default(qcd_solve_opts *opts);
+
+/* Solve D x = b to ||b - D x|| / ||b|| <= tol (recomputed in FP64 at exit;
+ * a restart from the true residual follows if the recursive residual
+ * drifted).  b, x: full-lattice complex128 [V][4][3], device or host memory
+ * (host buffers are staged through the device inside the call).  The
+ * nested scheme is Alg. 1 (flexible BiCGStab, FP64) around Alg. 2
+ * (BiCGStab on a unit-norm right-hand side from x = 0, lower precision).
+ * Blocks until the solve ends.  info may be NULL.
+ * Errors: QCD_ESTATE without clover term; QCD_ENOTCONV, QCD_EBREAKDOWN,
+ * QCD_ENONFINITE as the iteration ends; x then holds the last iterate. */
+int qcd_solve(qcd_ctx *ctx, const void *b, void *x, double tol, const qcd_solve_opts *opts,
+              qcd_solve_info *info);
+
+/* Kernel timing: when enabled, each launch of the fused MULT kernel
+ * (and of the other solver kernels) is bracketed by CUDA events on the
+ * context stream; qcd_kernel_stats sums them. */
+typedef enum {
+    QCD_K_MULT_F64 = 0,  /* MULT / D^ stencil kernels, by precision */
+    QCD_K_MULT_F32 = 1,
+    QCD_K_MULT_F16 = 2,
+    QCD_K_BLAS = 3,      /* fused BLAS-1 + reduction kernels */
+    QCD_K_OTHER = 4,
+    QCD_K_COUNT = 5
+} qcd_kernel_class;
+
+typedef struct {
+    long launches;
+    double ms;     /* summed device time */
+    double bytes;  /* summed algorithmic bytes */
+} qcd_kernel_stat;
+
+int qcd_set_profiling(qcd_ctx *ctx, int on);
+int qcd_kernel_stats(qcd_ctx *ctx, int kernel_class, qcd_kernel_stat *out);
+int qcd_reset_kernel_stats(qcd_ctx *ctx);
+
+/* Number of kernels this context has launched since it was created. */
+long qcd_launch_count(const qcd_ctx *ctx);
+
+/* Time the fused MULT kernel (Sec. II-B, out = F^-1 H_{p,1-p} in) alone on
+ * internal, already-resident buffers: `iters` launches on nrhs right-hand
+ * sides (nrhs <= 16) in precision prec, each launch bracketed by CUDA
+ * events and preceded by a write of 256 MB that evicts L2.  Returns the
+ * mean device time of one launch and its algorithmic bytes (each input
+ * read once, the output written once).  Synchronous.  Needs the clover
+ * term.  Allocates two nrhs-vector buffers and the flush buffer on first
+ * use. */
+int qcd_mult_benchmark(qcd_ctx *ctx, int prec, int nrhs, int iters, double *ms_per_launch,
+                       double *bytes_per_launch);
+
+const char *qcd_strerror(int status);
+const char *qcd_last_error(void);
+
+/* number of sites and of sites per parity of the context's lattice */
+long qcd_volume(const qcd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCD_GB300_H */

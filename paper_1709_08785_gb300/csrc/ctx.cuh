@@ -1,0 +1,175 @@
+// The library context and the internal interfaces between translation
+// units: field storage, solver state kept in device memory, the
+// single-pass grid reduction, and the kernel launchers.
+#pragma once
+
+#include <vector>
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+// An internal half-lattice vector in the site-blocked layout.
+struct HVec {
+    void *p = nullptr;
+    float *norm = nullptr;  // F16 only
+    int prec = QCD_F64;
+    SpinorPtr sp() const { return SpinorPtr{p, norm}; }
+};
+
+// Scalars of one BiCGStab level, kept in device memory so that no
+// iteration needs the host.  Complex numbers are (re, im) pairs.
+struct SolverState {
+    double sum[4];     // result of the last grid reduction
+    double rho0[2];
+    double alpha[2];
+    double omega[2];
+    double beta[2];
+    double rr;         // |r|^2 after the last update
+    double tol2;       // exit when |r|^2 < tol2
+    double tol2_rel;   // if > 0, FIN_INIT sets tol2 = tol2_rel * |r|^2
+    double norm2[4];   // saved squared norms (e.g. |p|^2, |b|^2)
+    double rt2;        // |r~|^2, for the breakdown test
+    double bd_eps;     // breakdown threshold on |rho1| / (|r~| |r|)
+    int iter;
+    int maxit;
+    int done;          // set once converged / capped / broken down
+    int status;        // qcd_status
+    int exit_half;     // 1: stopped after the first half-step of Alg. 2
+    int pad[3];
+};
+
+// Finaliser run by the last block of a reduction kernel.
+enum FinOp {
+    FIN_NONE = 0,
+    FIN_ALPHA,     // sum = <r~|q>            -> alpha = rho0 / <r~|q>
+    FIN_S,         // sum = |s|^2             -> half-step exit test
+    FIN_OMEGA,     // sum = <t|r>, |t|^2      -> omega
+    FIN_X,         // sum = |r|^2, <r~|r>     -> exit test, beta, rho0
+    FIN_INIT,      // sum = |r|^2             -> start: rho0 = rt2 = rr = norm2[1] = |r|^2 (and tol2)
+    FIN_RESTART,   // sum = |r|^2             -> restart from a recomputed residual
+    FIN_SETN = 16, // FIN_SETN + k: norm2[k] = sum[0]
+    FIN_ADDN = 20, // FIN_ADDN + k: norm2[k] += sum[0]
+};
+
+struct RedArgs {
+    double *partials = nullptr;  // [gridDim.x][4]
+    unsigned *counter = nullptr;
+    SolverState *st = nullptr;
+    int op = FIN_NONE;
+};
+
+enum StencilMode { M_HOP = 0, M_MULT = 1, M_DHAT = 2, M_SRC = 3, M_FULL = 4 };
+enum StencilRed { R_NONE = 0, R_DOT_AUX = 1, R_OMEGA = 2, R_NORM = 3 };
+
+}  // namespace qcd
+
+struct qcd_ctx {
+    qcd::Geom g;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+
+    // gauge links per parity of the base site
+    void *U64[2] = {nullptr, nullptr};
+    void *U32[2] = {nullptr, nullptr};
+    void *U16a[2] = {nullptr, nullptr};
+    void *U16b[2] = {nullptr, nullptr};
+    bool have_gauge = false;
+
+    // clover term F and inverse, [precision][parity]
+    void *C[3][2] = {};
+    void *Ci[3][2] = {};
+    bool have_clover = false;
+    double kappa = 0.0, csw = 0.0;
+
+    // reductions and solver scalars
+    double *partials = nullptr;
+    unsigned *counters = nullptr;          // one per reduction chain
+    qcd::SolverState *states = nullptr;    // device, NSTATES
+    qcd::SolverState *states_host = nullptr;  // pinned mirror
+    int *flag_dev = nullptr;
+    int partial_blocks = 0;
+
+    // workspace vectors, allocated on first use
+    std::vector<void *> pool;
+    qcd::HVec work[3][16];  // [precision][slot]
+    void *staging = nullptr;        // canonical full-lattice complex128 staging
+    size_t staging_bytes = 0;
+
+    // profiling
+    bool profiling = false;
+    struct Pending {
+        cudaEvent_t a, b;
+        int cls;
+        double bytes;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    int *prof_flags = nullptr;       // device: 1 if the launch returned early
+    int *prof_flags_host = nullptr;  // pinned mirror
+    qcd_kernel_stat stats[QCD_K_COUNT] = {};
+    long launches = 0;  // every kernel launch of this context
+
+    // qcd_mult_benchmark buffers
+    void *bench_buf = nullptr;
+    size_t bench_bytes = 0;
+    void *flush_buf = nullptr;
+};
+
+namespace qcd {
+
+constexpr int NSTATES = 8;
+constexpr int PROF_CAP = 1 << 16;  // profiled launches between two collections
+enum StateSlot { ST_OUTER = 0, ST_MID = 1, ST_INNER = 2, ST_AUX = 3 };
+
+// allocation helpers (api.cu)
+int dev_alloc(qcd_ctx *c, void **p, size_t bytes);
+size_t hvec_bytes(const Geom &g, int prec);
+int get_work(qcd_ctx *c, int prec, int slot, HVec *out);
+int ensure_staging(qcd_ctx *c, size_t bytes);
+
+// profiling (api.cu)
+struct ProfScope {
+    qcd_ctx *c;
+    int cls;
+    double bytes;
+    cudaEvent_t a = nullptr, b = nullptr;
+    int *flag = nullptr;  // device slot the kernel marks when it skips its work
+    ProfScope(qcd_ctx *c_, int cls_, double bytes_);
+    ~ProfScope();
+};
+int collect_profile(qcd_ctx *c);
+
+// gauge.cu
+int gauge_convert(qcd_ctx *c, const void *U_dev);
+int clover_build(qcd_ctx *c, double kappa, double csw);
+
+// stencil.cu
+struct StencilCall {
+    int prec = QCD_F64;
+    int mode = M_MULT;
+    int red = R_NONE;
+    int dagger = 0;
+    int out_par = 0;
+    HVec out, in, y, aux, z;
+    double a = 1.0, cc = 1.0, d = 0.0;
+    int nrhs = 1;
+    size_t rhs_stride = 0;  // sites*components stride between right-hand sides (elements of 16 bytes)
+    size_t norm_stride = 0;
+    RedArgs red_args;
+    const int *done = nullptr;
+};
+int launch_stencil(qcd_ctx *c, const StencilCall &s);
+double stencil_bytes(const qcd_ctx *c, const StencilCall &s);  // algorithmic bytes of one launch
+int fill_pattern(qcd_ctx *c, int prec, HVec v, int nrhs, size_t rhs_stride, int seed);
+
+// blas.cu -- conversions between canonical and internal layouts
+int canon_to_half(qcd_ctx *c, int prec, int src_is_f32, const void *src, int parity_full, HVec dst, int nrhs, size_t rhs_stride);
+int half_to_canon(qcd_ctx *c, int prec, int dst_is_f32, HVec src, void *dst, int parity_full, int nrhs, size_t rhs_stride);
+int clover_apply_half(qcd_ctx *c, int prec, int parity, int inverse, HVec in, HVec out, int nrhs, size_t rhs_stride);
+
+// solver.cu
+int solve(qcd_ctx *c, const void *b_dev, void *x_dev, double tol, const qcd_solve_opts &o, qcd_solve_info *info);
+
+}  // namespace qcd

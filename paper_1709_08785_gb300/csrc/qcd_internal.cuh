@@ -1,0 +1,427 @@
+// Internal definitions shared by the CUDA translation units of the clover
+// Wilson library: lattice geometry, the site-blocked structure-of-arrays
+// layouts in HBM, complex arithmetic, and the per-precision field accessors.
+//
+// Layouts (every field is split by parity; cb indexes the sites of one
+// parity, cb = lex/2 with lex = x + Lx*(y + Ly*(z + Lz*t))):
+//   sites are grouped in blocks of 32 (one warp); inside a block each
+//   16-byte component is stored for the 32 sites contiguously, so a warp
+//   reads one component of 32 neighbouring sites as one 512-byte burst.
+//   offset(cb, k) = ((cb >> 5) * NCOMP + k) * 32 + (cb & 31)
+//
+//   spinor  F64: 12 double2 (one complex each), index k = 3*spin + colour
+//           F32:  6 float4  (two complex each)
+//           F16:  3 uint4   (four complex each, IEEE half) + one float norm
+//                 per site; the stored halves are psi/norm, |.| <= 1
+//   link    F64: 9 double2, U_ij at k = 3*i + j (18 reals)
+//           F32: 3 float4, the first two columns a, b of U (12 reals,
+//                Sec. III-A "SU(3)-reconstruction"); U = (a, b, conj(a x b))
+//           F16: uint4 (a0 a1 a2 b0) + uint2 (b1 b2), 12 halves
+//           links are stored with the parity of their base site n; the
+//           four directions of a site share a block: NCOMP = 4*ncomp_link,
+//           k = mu*ncomp_link + component.
+//   clover  two 6x6 Hermitian blocks per site in the chiral (gamma5) basis,
+//           each as 6 real diagonal entries then the 15 complex entries
+//           below the diagonal, row by row: 72 reals per site
+//           F64: 36 double2, F32: 18 float4, F16: 9 uint4
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qcd.h"
+
+namespace qcd {
+
+constexpr int SB = 32;  // sites per block of the site-blocked layout
+
+__host__ __device__ inline long pad_sites(long n) { return (n + SB - 1) / SB * SB; }
+
+struct Geom {
+    int L[4];
+    int Lxh;      // Lx / 2
+    int st[4];    // lexicographic strides 1, Lx, Lx*Ly, Lx*Ly*Lz
+    int V;        // sites
+    int Vh;       // sites of one parity
+    int Vh_pad;   // Vh rounded up to SB
+    int t_bc;     // +1 periodic, -1 antiperiodic in time
+};
+
+__device__ __forceinline__ size_t soa(int cb, int ncomp, int k)
+{
+    return ((size_t)(cb >> 5) * ncomp + k) * SB + (cb & 31);
+}
+
+// coordinates of the cb-th site of parity p
+__device__ __forceinline__ void site_coords(const Geom &g, int parity, int cb, int c[4])
+{
+    int r = cb / g.Lxh;
+    int xh = cb - r * g.Lxh;
+    c[1] = r % g.L[1];
+    r /= g.L[1];
+    c[2] = r % g.L[2];
+    c[3] = r / g.L[2];
+    c[0] = 2 * xh + ((parity + c[1] + c[2] + c[3]) & 1);
+}
+
+__device__ __forceinline__ int lex_of(const Geom &g, const int c[4])
+{
+    return c[0] + g.st[1] * c[1] + g.st[2] * c[2] + g.st[3] * c[3];
+}
+
+// lexicographic index of the neighbour n + sign*mu
+__device__ __forceinline__ int lex_hop(const Geom &g, int lex, const int c[4], int mu, int sign)
+{
+    if (sign > 0) return (c[mu] == g.L[mu] - 1) ? lex - g.st[mu] * (g.L[mu] - 1) : lex + g.st[mu];
+    return (c[mu] == 0) ? lex + g.st[mu] * (g.L[mu] - 1) : lex - g.st[mu];
+}
+
+// ---------------------------------------------------------------- complex
+template <class T>
+struct cx {
+    T r, i;
+};
+
+template <class T>
+__device__ __forceinline__ cx<T> mk(T r, T i) { return cx<T>{r, i}; }
+template <class T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.r + b.r, a.i + b.i}; }
+template <class T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.r - b.r, a.i - b.i}; }
+template <class T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a) { return {-a.r, -a.i}; }
+template <class T>
+__device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+template <class T>
+__device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.r, s * a.i}; }
+template <class T>
+__device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.r, -a.i}; }
+// i*a and -i*a
+template <class T>
+__device__ __forceinline__ cx<T> ti(cx<T> a) { return {-a.i, a.r}; }
+template <class T>
+__device__ __forceinline__ cx<T> tmi(cx<T> a) { return {a.i, -a.r}; }
+// a += b*c ; a += conj(b)*c
+template <class T>
+__device__ __forceinline__ void fma_(cx<T> &a, cx<T> b, cx<T> c)
+{
+    a.r = fma(b.r, c.r, a.r);
+    a.r = fma(-b.i, c.i, a.r);
+    a.i = fma(b.r, c.i, a.i);
+    a.i = fma(b.i, c.r, a.i);
+}
+template <class T>
+__device__ __forceinline__ void fmac_(cx<T> &a, cx<T> b, cx<T> c)
+{
+    a.r = fma(b.r, c.r, a.r);
+    a.r = fma(b.i, c.i, a.r);
+    a.i = fma(b.r, c.i, a.i);
+    a.i = fma(-b.i, c.r, a.i);
+}
+
+template <class T>
+struct Spinor {
+    cx<T> s[4][3];
+};
+
+template <class T>
+struct Link {
+    cx<T> u[3][3];
+};
+
+// ---------------------------------------------------------------- fields
+// Raw pointers to one parity of a field, by precision.
+struct SpinorPtr {
+    void *p;       // double2* / float4* / uint4*
+    float *norm;   // F16 only
+};
+
+struct GaugePtr {
+    const void *a[2];  // per parity of the base site
+    const void *b[2];  // F16 only: the uint2 part
+};
+
+struct CloverPtr {
+    const void *p[2];  // per parity
+};
+
+template <int P>
+struct Prec;
+
+template <>
+struct Prec<QCD_F64> {
+    using T = double;
+    static constexpr int SP_NC = 12, LK_NC = 9, CL_NC = 36;
+
+    static __device__ __forceinline__ void load(const SpinorPtr &v, int cb, Spinor<T> &s)
+    {
+        const double2 *p = (const double2 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 d = __ldg(p + soa(cb, 12, k));
+            s.s[k / 3][k % 3] = mk(d.x, d.y);
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorPtr &v, int cb, const Spinor<T> &s)
+    {
+        double2 *p = (double2 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[soa(cb, 12, k)] = make_double2(s.s[k / 3][k % 3].r, s.s[k / 3][k % 3].i);
+    }
+    static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
+    {
+        const double2 *p = (const double2 *)g.a[par];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double2 d = __ldg(p + soa(cb, 36, mu * 9 + k));
+            U.u[k / 3][k % 3] = mk(d.x, d.y);
+        }
+    }
+    // one 6x6 block: d[6] real diagonal, o[15] complex lower triangle
+    static __device__ __forceinline__ void load_clover(const CloverPtr &c, int par, int cb, int blk, T d[6], cx<T> o[15])
+    {
+        const double2 *p = (const double2 *)c.p[par];
+        const int k0 = blk * 18;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double2 v = __ldg(p + soa(cb, 36, k0 + k));
+            d[2 * k] = v.x;
+            d[2 * k + 1] = v.y;
+        }
+#pragma unroll
+        for (int k = 0; k < 15; ++k) {
+            double2 v = __ldg(p + soa(cb, 36, k0 + 3 + k));
+            o[k] = mk(v.x, v.y);
+        }
+    }
+};
+
+__device__ __forceinline__ void reconstruct(Link<float> &U)
+{
+    // third column c = conj(a x b)
+    cx<float> a0 = U.u[0][0], a1 = U.u[1][0], a2 = U.u[2][0];
+    cx<float> b0 = U.u[0][1], b1 = U.u[1][1], b2 = U.u[2][1];
+    U.u[0][2] = conj(a1 * b2 - a2 * b1);
+    U.u[1][2] = conj(a2 * b0 - a0 * b2);
+    U.u[2][2] = conj(a0 * b1 - a1 * b0);
+}
+
+template <>
+struct Prec<QCD_F32> {
+    using T = float;
+    static constexpr int SP_NC = 6, LK_NC = 3, CL_NC = 18;
+
+    static __device__ __forceinline__ void load(const SpinorPtr &v, int cb, Spinor<T> &s)
+    {
+        const float4 *p = (const float4 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 f = __ldg(p + soa(cb, 6, k));
+            s.s[(2 * k) / 3][(2 * k) % 3] = mk(f.x, f.y);
+            s.s[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(f.z, f.w);
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorPtr &v, int cb, const Spinor<T> &s)
+    {
+        float4 *p = (float4 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            cx<float> a = s.s[(2 * k) / 3][(2 * k) % 3], b = s.s[(2 * k + 1) / 3][(2 * k + 1) % 3];
+            p[soa(cb, 6, k)] = make_float4(a.r, a.i, b.r, b.i);
+        }
+    }
+    static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
+    {
+        const float4 *p = (const float4 *)g.a[par];
+        float4 f0 = __ldg(p + soa(cb, 12, mu * 3 + 0));
+        float4 f1 = __ldg(p + soa(cb, 12, mu * 3 + 1));
+        float4 f2 = __ldg(p + soa(cb, 12, mu * 3 + 2));
+        U.u[0][0] = mk(f0.x, f0.y);
+        U.u[1][0] = mk(f0.z, f0.w);
+        U.u[2][0] = mk(f1.x, f1.y);
+        U.u[0][1] = mk(f1.z, f1.w);
+        U.u[1][1] = mk(f2.x, f2.y);
+        U.u[2][1] = mk(f2.z, f2.w);
+        reconstruct(U);
+    }
+    static __device__ __forceinline__ void load_clover(const CloverPtr &c, int par, int cb, int blk, T d[6], cx<T> o[15])
+    {
+        const float4 *p = (const float4 *)c.p[par];
+        float r[36];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float4 f = __ldg(p + soa(cb, 18, blk * 9 + k));
+            r[4 * k] = f.x;
+            r[4 * k + 1] = f.y;
+            r[4 * k + 2] = f.z;
+            r[4 * k + 3] = f.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) d[k] = r[k];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) o[k] = mk(r[6 + 2 * k], r[7 + 2 * k]);
+    }
+};
+
+__device__ __forceinline__ cx<float> h2c(__half2 h) { float2 f = __half22float2(h); return mk(f.x, f.y); }
+__device__ __forceinline__ __half2 c2h(cx<float> c) { return __floats2half2_rn(c.r, c.i); }
+
+__device__ __forceinline__ __half2 u2h(unsigned u) { return *reinterpret_cast<__half2 *>(&u); }
+__device__ __forceinline__ unsigned h2u(__half2 h) { return *reinterpret_cast<unsigned *>(&h); }
+
+template <>
+struct Prec<QCD_F16> {
+    using T = float;  // FP16 storage, FP32 arithmetic
+    static constexpr int SP_NC = 3, LK_NC = 1, CL_NC = 9;
+
+    static __device__ __forceinline__ void load(const SpinorPtr &v, int cb, Spinor<T> &s)
+    {
+        const uint4 *p = (const uint4 *)v.p;
+        const float nrm = __ldg(v.norm + cb);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 q = __ldg(p + soa(cb, 3, k));
+            unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int c = 4 * k + j;
+                cx<float> z = h2c(u2h(w[j]));
+                s.s[c / 3][c % 3] = mk(z.r * nrm, z.i * nrm);
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(const SpinorPtr &v, int cb, const Spinor<T> &s)
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) m = fmaxf(m, fmaxf(fabsf(s.s[a][i].r), fabsf(s.s[a][i].i)));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint4 *p = (uint4 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            unsigned w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int c = 4 * k + j;
+                w[j] = h2u(c2h(mk(s.s[c / 3][c % 3].r * inv, s.s[c / 3][c % 3].i * inv)));
+            }
+            p[soa(cb, 3, k)] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        v.norm[cb] = m;
+    }
+    static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
+    {
+        uint4 qa = __ldg((const uint4 *)g.a[par] + soa(cb, 4, mu));
+        uint2 qb = __ldg((const uint2 *)g.b[par] + soa(cb, 4, mu));
+        U.u[0][0] = h2c(u2h(qa.x));
+        U.u[1][0] = h2c(u2h(qa.y));
+        U.u[2][0] = h2c(u2h(qa.z));
+        U.u[0][1] = h2c(u2h(qa.w));
+        U.u[1][1] = h2c(u2h(qb.x));
+        U.u[2][1] = h2c(u2h(qb.y));
+        reconstruct(U);
+    }
+    static __device__ __forceinline__ void load_clover(const CloverPtr &c, int par, int cb, int blk, T d[6], cx<T> o[15])
+    {
+        // 36 halves per block: 4.5 uint4; block 0 uses uint4 0..4 (first
+        // half of 4), block 1 the second half of 4 and 5..8
+        const uint4 *p = (const uint4 *)c.p[par];
+        float r[36];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if (blk == 0 && k > 4) continue;
+            if (blk == 1 && k < 4) continue;
+            uint4 q = __ldg(p + soa(cb, 9, k));
+            unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 f = __half22float2(u2h(w[j]));
+                int e = 8 * k + 2 * j - blk * 36;  // element index within the block
+                if (e >= 0 && e < 36) r[e] = f.x;
+                if (e + 1 >= 0 && e + 1 < 36) r[e + 1] = f.y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) d[k] = r[k];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) o[k] = mk(r[6 + 2 * k], r[7 + 2 * k]);
+    }
+};
+
+// ---------------------------------------------------------------- clover
+// y = A x for a 6x6 Hermitian block (d real diagonal, o lower triangle,
+// row-major: o[0]=(1,0), o[1]=(2,0), o[2]=(2,1), o[3]=(3,0), ...).
+template <class T>
+__device__ __forceinline__ void herm6(const T d[6], const cx<T> o[15], const cx<T> x[6], cx<T> y[6])
+{
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] = mk(d[i] * x[i].r, d[i] * x[i].i);
+    int k = 0;
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            fma_(y[i], o[k], x[j]);   // A_ij x_j
+            fmac_(y[j], o[k], x[i]);  // A_ji = conj(A_ij)
+            ++k;
+        }
+}
+
+// Apply the clover (or its inverse) stored as two chiral 6x6 blocks to a
+// spinor in the Dirac basis.  With gamma5 = -[[0,1],[1,0]] the chiral
+// components are chi_+ = (psi_up - psi_dn)/sqrt2 (gamma5 = +1) and
+// chi_- = (psi_up + psi_dn)/sqrt2; the 1/sqrt2 factors are combined into
+// the final 1/2.
+template <int P>
+__device__ __forceinline__ void apply_clover(const CloverPtr &c, int par, int cb, Spinor<typename Prec<P>::T> &s)
+{
+    using T = typename Prec<P>::T;
+    cx<T> xp[6], xm[6], yp[6], ym[6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            xp[3 * a + i] = s.s[a][i] - s.s[a + 2][i];
+            xm[3 * a + i] = s.s[a][i] + s.s[a + 2][i];
+        }
+    {
+        T d[6];
+        cx<T> o[15];
+        Prec<P>::load_clover(c, par, cb, 0, d, o);
+        herm6(d, o, xp, yp);
+    }
+    {
+        T d[6];
+        cx<T> o[15];
+        Prec<P>::load_clover(c, par, cb, 1, d, o);
+        herm6(d, o, xm, ym);
+    }
+    const T h = T(0.5);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            s.s[a][i] = h * (yp[3 * a + i] + ym[3 * a + i]);
+            s.s[a + 2][i] = h * (ym[3 * a + i] - yp[3 * a + i]);
+        }
+}
+
+// ---------------------------------------------------------------- helpers
+#define QCD_CUDA_CHECK(x)                                 \
+    do {                                                  \
+        cudaError_t e__ = (x);                            \
+        if (e__ != cudaSuccess) {                         \
+            qcd::set_cuda_error(e__, #x, __FILE__, __LINE__); \
+            return QCD_ECUDA;                             \
+        }                                                 \
+    } while (0)
+
+void set_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void set_error_message(const char *fmt, ...);
+
+inline unsigned nblocks(long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace qcd

@@ -1,0 +1,189 @@
+// Single-pass grid reduction with a deterministic order, and the BiCGStab
+// scalar updates that its last block performs.
+//
+// Each block reduces its threads' values (warp shuffles, then one warp over
+// the warp sums), writes one partial per block, and takes a ticket; the
+// block that takes the last ticket adds the partials in block order and
+// runs the finaliser on the solver state.  The sum order depends only on the
+// launch shape, so results repeat bit for bit from run to run.  This replaces
+// the paper's MPI_Allreduce of every dot product and norm (Sec. IV-B).
+#pragma once
+
+#include "ctx.cuh"
+
+namespace qcd {
+
+__device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
+
+// The scalar recurrences of BiCGStab (Alg. 2, with alpha = rho0/<r~|q> and
+// beta = (rho1/rho0)(alpha/omega), the standard reading of the printed
+// formulas), run by one thread.
+__device__ inline void finalize(int op, SolverState *st)
+{
+    const double *s = st->sum;
+    switch (op) {
+    case FIN_ALPHA: {
+        const double dr = s[0], di = s[1];
+        const double den = dr * dr + di * di;
+        st->iter += 1;
+        if (!(den > 0.0) || !finite_d(den)) {
+            st->done = 1;
+            st->status = finite_d(den) ? QCD_EBREAKDOWN : QCD_ENONFINITE;
+            break;
+        }
+        st->alpha[0] = (st->rho0[0] * dr + st->rho0[1] * di) / den;
+        st->alpha[1] = (st->rho0[1] * dr - st->rho0[0] * di) / den;
+        break;
+    }
+    case FIN_S:
+        st->rr = s[0];
+        if (!finite_d(s[0])) {
+            st->done = 1;
+            st->status = QCD_ENONFINITE;
+        } else if (s[0] < st->tol2) {
+            st->done = 1;
+            st->status = QCD_OK;
+            st->exit_half = 1;
+        }
+        break;
+    case FIN_OMEGA: {
+        const double tt = s[2];
+        if (!(tt > 0.0) || !finite_d(tt) || !finite_d(s[0]) || !finite_d(s[1])) {
+            st->done = 1;
+            st->status = finite_d(tt) ? QCD_EBREAKDOWN : QCD_ENONFINITE;
+            st->exit_half = 1;
+            break;
+        }
+        st->omega[0] = s[0] / tt;
+        st->omega[1] = s[1] / tt;
+        if (st->omega[0] == 0.0 && st->omega[1] == 0.0) {
+            st->done = 1;
+            st->status = QCD_EBREAKDOWN;
+            st->exit_half = 1;
+        }
+        break;
+    }
+    case FIN_X: {
+        const double rr = s[0], r1r = s[1], r1i = s[2];
+        st->rr = rr;
+        st->exit_half = 0;
+        if (!finite_d(rr) || !finite_d(r1r) || !finite_d(r1i)) {
+            st->done = 1;
+            st->status = QCD_ENONFINITE;
+        } else if (rr < st->tol2) {
+            st->done = 1;
+            st->status = QCD_OK;
+        } else if (sqrt(r1r * r1r + r1i * r1i) <= st->bd_eps * sqrt(st->rt2 * rr)) {
+            st->done = 1;
+            st->status = QCD_EBREAKDOWN;
+        } else if (st->iter >= st->maxit) {
+            st->done = 1;
+            st->status = QCD_ENOTCONV;
+        } else {
+            // beta = (rho1/rho0) * (alpha/omega)
+            const double d0 = st->rho0[0] * st->rho0[0] + st->rho0[1] * st->rho0[1];
+            const double qr = (r1r * st->rho0[0] + r1i * st->rho0[1]) / d0;
+            const double qi = (r1i * st->rho0[0] - r1r * st->rho0[1]) / d0;
+            const double d1 = st->omega[0] * st->omega[0] + st->omega[1] * st->omega[1];
+            const double ar = (st->alpha[0] * st->omega[0] + st->alpha[1] * st->omega[1]) / d1;
+            const double ai = (st->alpha[1] * st->omega[0] - st->alpha[0] * st->omega[1]) / d1;
+            st->beta[0] = qr * ar - qi * ai;
+            st->beta[1] = qr * ai + qi * ar;
+            st->rho0[0] = r1r;
+            st->rho0[1] = r1i;
+        }
+        break;
+    }
+    case FIN_INIT:
+    case FIN_RESTART:
+        // r = r~ = p = b: rho0 = |b|^2; a zero right-hand side is converged
+        if (op == FIN_INIT && st->tol2_rel > 0.0) st->tol2 = st->tol2_rel * s[0];
+        st->norm2[1] = s[0];
+        st->rr = s[0];
+        st->rt2 = s[0];
+        st->rho0[0] = s[0];
+        st->rho0[1] = 0.0;
+        st->exit_half = 0;
+        if (!finite_d(s[0])) {
+            st->done = 1;
+            st->status = QCD_ENONFINITE;
+        } else if (s[0] <= st->tol2 || s[0] == 0.0) {
+            st->done = 1;
+            st->status = QCD_OK;
+        } else {
+            st->done = 0;
+            st->status = QCD_OK;
+        }
+        break;
+    default:
+        if (op >= FIN_SETN && op < FIN_SETN + 4) st->norm2[op - FIN_SETN] = s[0];
+        else if (op >= FIN_ADDN && op < FIN_ADDN + 4) st->norm2[op - FIN_ADDN] += s[0];
+        break;
+    }
+}
+
+// Reduce N doubles over the grid; blocks may be 1-D or 2-D.
+template <int N>
+__device__ __forceinline__ void grid_reduce(double v[N], const RedArgs &ra)
+{
+    __shared__ double sh[32][4];
+    __shared__ int last;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthr = blockDim.x * blockDim.y;
+    const int lane = tid & 31, wid = tid >> 5, nw = (nthr + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[wid][k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            double t = lane < nw ? sh[lane][k] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+            v[k] = t;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) ra.partials[(size_t)blockIdx.x * 4 + k] = v[k];
+            __threadfence();
+            unsigned t = atomicAdd(ra.counter, 1u);
+            last = (t == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) s[k] = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += nthr)
+#pragma unroll
+        for (int k = 0; k < N; ++k) s[k] += __ldcg(ra.partials + (size_t)b * 4 + k);
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], off);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[wid][k] = s[k];
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 0; k < N; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[w][k];
+            ra.st->sum[k] = t;
+        }
+        for (int k = N; k < 4; ++k) ra.st->sum[k] = 0.0;
+        finalize(ra.op, ra.st);
+        *ra.counter = 0u;
+        __threadfence();
+    }
+}
+
+}  // namespace qcd

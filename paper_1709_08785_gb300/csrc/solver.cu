@@ -1,0 +1,503 @@
+// Solver drivers: the nested BiCGStab of Algs. 1-2 (FP64 flexible outer
+// iteration around a lower-precision BiCGStab on a unit-norm right-hand
+// side), its three-level form (FP64 / FP32 / FP16 storage), the plain FP64
+// BiCGStab on D^_ee, and the unpreconditioned FP64 BiCGStab on D.
+//
+// Every scalar lives in device memory (SolverState); the host only queues
+// kernels.  A lower level's iterations are queued in chunks whose size is
+// predicted from the convergence rate so far; kernels queued past
+// convergence see the state marked done and return at once.  The host reads
+// the state back once per chunk and once per half-iteration of the FP64
+// level.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "blas.cuh"
+
+namespace qcd {
+
+namespace {
+
+// bd_eps of the breakdown test |rho1| <= bd_eps |r~| |r| (the paper has
+// none; FP64 levels use 1e-30, lower precisions 1e-12)
+constexpr double BD_EPS_F64 = 1e-30;
+constexpr double BD_EPS_LOW = 1e-12;
+
+struct Level {
+    int prec = QCD_F64;
+    HVec x, r, rt, p, q, t, v, tmp;  // tmp: odd-parity workspace of D^
+    SolverState *st = nullptr;       // device
+    int slot = 0;                    // index into the state arrays
+};
+
+int read_state(qcd_ctx *c, int slot, SolverState *out)
+{
+    QCD_CUDA_CHECK(cudaMemcpyAsync(c->states_host + slot, c->states + slot, sizeof(SolverState), cudaMemcpyDeviceToHost,
+                                   c->stream));
+    QCD_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    *out = c->states_host[slot];
+    return QCD_OK;
+}
+
+#define TRY(x)                     \
+    do {                           \
+        int rc__ = (x);            \
+        if (rc__ != QCD_OK) return rc__; \
+    } while (0)
+
+// out = D^ in = in - kappa^2 F_ee^-1 H_eo F_oo^-1 H_oe in (Eq. 8) with a
+// reduction fused into the second half.
+int dhat(qcd_ctx *c, int prec, HVec in, HVec out, HVec tmp, int red, HVec aux, SolverState *st, int fin,
+         const int *done)
+{
+    StencilCall s1;
+    s1.prec = prec;
+    s1.mode = M_MULT;
+    s1.out_par = 1;
+    s1.out = tmp;
+    s1.in = in;
+    s1.done = done;
+    TRY(launch_stencil(c, s1));
+    StencilCall s2;
+    s2.prec = prec;
+    s2.mode = M_DHAT;
+    s2.out_par = 0;
+    s2.out = out;
+    s2.in = tmp;
+    s2.y = in;
+    s2.a = 1.0;
+    s2.cc = -c->kappa * c->kappa;
+    s2.red = red;
+    s2.aux = aux;
+    s2.red_args.partials = c->partials;
+    s2.red_args.counter = c->counters;
+    s2.red_args.st = st;
+    s2.red_args.op = fin;
+    s2.done = done;
+    return launch_stencil(c, s2);
+}
+
+// One iteration of Alg. 2 on level L (all in L.prec).
+int bicg_iteration(qcd_ctx *c, Level &L)
+{
+    const int n = c->g.Vh_pad;
+    const int *done = &L.st->done;
+    TRY(dhat(c, L.prec, L.p, L.q, L.tmp, R_DOT_AUX, L.rt, L.st, FIN_ALPHA, done));  // q = D^ p, alpha
+    TRY(blas_update_s(c, L.prec, n, L.r, L.q, L.st));                              // s = r - alpha q
+    TRY(dhat(c, L.prec, L.r, L.t, L.tmp, R_OMEGA, L.r, L.st, FIN_OMEGA, done));     // t = D^ s, omega
+    TRY(blas_update_x(c, L.prec, n, L.x, L.p, L.r, L.t, L.rt, L.st));              // x, r, beta
+    TRY(blas_update_p(c, L.prec, n, L.p, L.r, L.q, L.st, FIN_NONE));               // p
+    return QCD_OK;
+}
+
+// Run Alg. 2 iterations on L until its state is done; returns the
+// iterations executed.
+int run_bicg(qcd_ctx *c, Level &L, SolverState *final_state)
+{
+    SolverState h;
+    int queued = 0;
+    int chunk = 3;
+    double rr0 = -1.0;
+    for (;;) {
+        for (int k = 0; k < chunk; ++k) TRY(bicg_iteration(c, L));
+        queued += chunk;
+        TRY(read_state(c, L.slot, &h));
+        if (rr0 < 0.0) rr0 = h.rr > 0 ? h.rr : 1.0;
+        if (h.done) break;
+        if (queued > h.maxit + 8) {  // cannot happen: FIN_X caps at maxit
+            set_error_message("iteration queue overran the cap");
+            return QCD_ETIMEOUT;
+        }
+        // predict the remaining iterations from the mean contraction so far
+        int pred = 8;
+        if (h.iter > 0 && h.rr > 0.0 && h.rr < rr0 && h.tol2 > 0.0) {
+            const double rate = std::log(h.rr / rr0) / h.iter;  // < 0
+            pred = (int)std::ceil(std::log(h.tol2 / h.rr) / rate);
+        }
+        if (pred < 2) pred = 2;
+        if (pred > 64) pred = 64;
+        if (pred > h.maxit - h.iter + 1) pred = h.maxit - h.iter + 1;
+        chunk = pred < 1 ? 1 : pred;
+    }
+    TRY(blas_finish_half(c, L.prec, c->g.Vh_pad, L.x, L.p, L.st));
+    *final_state = h;
+    return QCD_OK;
+}
+
+// ||b - D x|| / ||b|| from norm2[2] = |b - D x|^2 and norm2[0] = |b|^2;
+// non-finite if either is; 0 for b = 0 (x = 0 is then exact)
+double resid_ratio(const SolverState &a)
+{
+    const double b2 = a.norm2[0], r2 = a.norm2[2];
+    if (!std::isfinite(b2) || !std::isfinite(r2)) return NAN;
+    if (b2 == 0.0) return r2 == 0.0 ? 0.0 : INFINITY;
+    return std::sqrt(r2 / b2);
+}
+
+struct Solver {
+    qcd_ctx *c;
+    qcd_solve_opts o;
+    qcd_solve_info info;
+    Level lv[3];  // 0: FP64, 1: FP32, 2: FP16
+    HVec be, bo, bhat, xo, re, ro;
+    SolverState *aux;
+};
+
+int get_level(qcd_ctx *c, Level &L, int prec, int first_slot, int state_slot)
+{
+    L.prec = prec;
+    HVec *v[8] = {&L.x, &L.r, &L.rt, &L.p, &L.q, &L.t, &L.v, &L.tmp};
+    for (int k = 0; k < 8; ++k) TRY(get_work(c, prec, first_slot + k, v[k]));
+    L.slot = state_slot;
+    L.st = c->states + state_slot;
+    return QCD_OK;
+}
+
+// v = M src: the lower levels approximately solve D^ v = src (Alg. 2, and
+// for three levels the flexible FP32 middle level around it).
+int precondition(Solver &S, int level, HVec src, int src_prec, const double *src_norm2, HVec v, const int *done);
+
+// Alg. 1 on level `lev` (flexible BiCGStab, preconditioned by the level
+// below), from the state already initialised by blas_init.
+int flexible(Solver &S, int lev)
+{
+    qcd_ctx *c = S.c;
+    Level &L = S.lv[lev];
+    const int n = c->g.Vh_pad;
+    const int *done = &L.st->done;
+    SolverState h;
+    TRY(read_state(c, L.slot, &h));
+    if (h.done) return QCD_OK;
+    for (;;) {
+        TRY(precondition(S, lev + 1, L.p, L.prec, &L.st->norm2[1], L.v, done));      // v = M p
+        TRY(dhat(c, L.prec, L.v, L.q, L.tmp, R_DOT_AUX, L.rt, L.st, FIN_ALPHA, done));  // q = D^ v, alpha
+        TRY(blas_flex1(c, L.prec, n, L.x, L.v, L.r, L.q, L.st));                       // x, r, |r|
+        S.info.dhat_applies[L.prec] += 1;
+        TRY(read_state(c, L.slot, &h));
+        if (h.done) break;
+        TRY(precondition(S, lev + 1, L.r, L.prec, &L.st->rr, L.v, done));                // v = M r
+        TRY(dhat(c, L.prec, L.v, L.t, L.tmp, R_OMEGA, L.r, L.st, FIN_OMEGA, done));      // t = D^ v, omega
+        TRY(blas_flex2(c, L.prec, n, L.x, L.v, L.r, L.t, L.rt, L.st));                  // x, r, beta
+        TRY(blas_update_p(c, L.prec, n, L.p, L.r, L.q, L.st, FIN_SETN + 1));             // p, |p|
+        S.info.dhat_applies[L.prec] += 1;
+        TRY(read_state(c, L.slot, &h));
+        if (h.done) break;
+    }
+    return QCD_OK;
+}
+
+int precondition(Solver &S, int level, HVec src, int src_prec, const double *src_norm2, HVec v, const int *done)
+{
+    qcd_ctx *c = S.c;
+    Level &L = S.lv[level];
+    const int n = c->g.Vh_pad;
+    const bool last = level == S.o.precision_levels - 1;
+    const double tol = S.o.inner_tol[level - 1];
+    TRY(state_init(c, L.st, tol * tol, 0.0, S.o.max_inner[level - 1], BD_EPS_LOW, 1));
+    TRY(blas_inner_init(c, src_prec, L.prec, n, src, src_norm2, L.r, L.rt, L.p, L.x, done));
+    SolverState h;
+    if (last) {
+        TRY(run_bicg(c, L, &h));
+        S.info.inner_iters[level - 1] += h.iter;
+        S.info.dhat_applies[L.prec] += 2L * h.iter - h.exit_half;
+    } else {
+        // the middle level is itself flexible (Alg. 1 in FP32) and needs
+        // norm2[1] = |p|^2 = 1 of its unit-norm start
+        TRY(flexible(S, level));
+        TRY(read_state(c, L.slot, &h));
+        S.info.inner_iters[level - 1] += h.iter;
+    }
+    return blas_lift(c, L.prec, src_prec, n, L.x, v, src_norm2, done);
+}
+
+int residual_eo(Solver &S, HVec xe, HVec out, SolverState *st, int fin)
+{
+    // out = b^ - D^ x_e = b^ - x_e + kappa^2 H~_eo H~_oe x_e
+    qcd_ctx *c = S.c;
+    Level &L = S.lv[0];
+    StencilCall s1;
+    s1.prec = QCD_F64;
+    s1.mode = M_MULT;
+    s1.out_par = 1;
+    s1.out = L.tmp;
+    s1.in = xe;
+    TRY(launch_stencil(c, s1));
+    StencilCall s2;
+    s2.prec = QCD_F64;
+    s2.mode = M_DHAT;
+    s2.out_par = 0;
+    s2.out = out;
+    s2.in = L.tmp;
+    s2.y = xe;
+    s2.a = -1.0;
+    s2.cc = c->kappa * c->kappa;
+    s2.z = S.bhat;
+    s2.d = 1.0;
+    s2.red = R_NORM;
+    s2.red_args = RedArgs{c->partials, c->counters, st, fin};
+    return launch_stencil(c, s2);
+}
+
+// ||b - D x||^2 of the full solution (x_e, x_o) into aux->norm2[2]
+int true_residual(Solver &S, HVec xe, HVec xo)
+{
+    qcd_ctx *c = S.c;
+    for (int par = 0; par < 2; ++par) {
+        StencilCall s;
+        s.prec = QCD_F64;
+        s.mode = M_FULL;
+        s.out_par = par;
+        s.out = par ? S.ro : S.re;
+        s.in = par ? xe : xo;
+        s.y = par ? xo : xe;
+        s.a = -1.0;
+        s.cc = c->kappa;
+        s.z = par ? S.bo : S.be;
+        s.d = 1.0;
+        s.red = R_NORM;
+        s.red_args = RedArgs{c->partials, c->counters, S.aux, par ? FIN_ADDN + 2 : FIN_SETN + 2};
+        TRY(launch_stencil(c, s));
+    }
+    return QCD_OK;
+}
+
+int solve_eo(Solver &S, const void *b, void *x, double tol)
+{
+    qcd_ctx *c = S.c;
+    const int n = c->g.Vh_pad;
+    Level &O = S.lv[0];
+    TRY(get_work(c, QCD_F64, 0, &S.be));
+    TRY(get_work(c, QCD_F64, 1, &S.bo));
+    TRY(get_work(c, QCD_F64, 2, &S.bhat));
+    TRY(get_work(c, QCD_F64, 3, &S.xo));
+    TRY(get_work(c, QCD_F64, 4, &S.re));
+    TRY(get_work(c, QCD_F64, 5, &S.ro));
+    TRY(get_level(c, O, QCD_F64, 6, ST_OUTER));
+    if (S.o.precision_levels >= 2) TRY(get_level(c, S.lv[1], QCD_F32, 0, ST_MID));
+    if (S.o.precision_levels >= 3) TRY(get_level(c, S.lv[2], QCD_F16, 0, ST_INNER));
+    S.aux = c->states + ST_AUX;
+
+    // b -> (b_e, b_o); |b|^2
+    TRY(canon_to_half(c, QCD_F64, 0, b, 0, S.be, 1, 0));
+    TRY(canon_to_half(c, QCD_F64, 0, b, 1, S.bo, 1, 0));
+    TRY(state_init(c, S.aux, 0.0, 0.0, 0, 0.0, 0));
+    TRY(blas_norm2(c, QCD_F64, n, S.be, S.aux, FIN_SETN + 0));
+    TRY(blas_norm2(c, QCD_F64, n, S.bo, S.aux, FIN_ADDN + 0));
+    // b^_e = F_ee^-1 (b_e + kappa H_eo F_oo^-1 b_o)   (Eq. 6, Alg. 1 line 3)
+    TRY(clover_apply_half(c, QCD_F64, 1, 1, S.bo, O.tmp, 1, 0));
+    {
+        StencilCall s;
+        s.prec = QCD_F64;
+        s.mode = M_SRC;
+        s.out_par = 0;
+        s.out = S.bhat;
+        s.in = O.tmp;
+        s.y = S.be;
+        s.a = 1.0;
+        s.cc = c->kappa;
+        TRY(launch_stencil(c, s));
+    }
+    // the recursive residual |r^_e| is driven below tol |b| / 2: the full
+    // residual is F_ee r^_e with |F_ee| close to one; the true residual
+    // is checked at the end and the iteration restarted from it if needed
+    const int maxit = S.o.max_outer;
+    TRY(state_init(c, O.st, 0.0, 0.0, maxit, BD_EPS_F64, 0));
+    TRY(set_tol2(c, O.st, S.aux, 0, 0.25 * tol * tol));
+    if (S.o.use_x0) {
+        TRY(canon_to_half(c, QCD_F64, 0, x, 0, O.x, 1, 0));
+        TRY(residual_eo(S, O.x, O.r, O.st, FIN_NONE));
+        TRY(blas_init(c, QCD_F64, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_INIT));
+    } else {
+        TRY(blas_init(c, QCD_F64, n, S.bhat, O.r, O.rt, O.p, O.x, 1, O.st, FIN_INIT));
+    }
+    SolverState h, ha;
+    int status = QCD_OK;
+    for (int restart = 0;; ++restart) {
+        if (S.o.precision_levels == 1) {
+            TRY(run_bicg(c, O, &h));
+            S.info.dhat_applies[QCD_F64] += 2L * h.iter - h.exit_half;
+        } else {
+            TRY(flexible(S, 0));
+            TRY(read_state(c, O.slot, &h));
+        }
+        S.info.outer_iters = h.iter;
+        status = h.status;
+        // x_o = F_oo^-1 (b_o + kappa H_oe x_e)   (Eq. 7, Alg. 1 line 19)
+        StencilCall s;
+        s.prec = QCD_F64;
+        s.mode = M_SRC;
+        s.out_par = 1;
+        s.out = S.xo;
+        s.in = O.x;
+        s.y = S.bo;
+        s.a = 1.0;
+        s.cc = c->kappa;
+        TRY(launch_stencil(c, s));
+        TRY(true_residual(S, O.x, S.xo));
+        TRY(read_state(c, ST_AUX, &ha));
+        S.info.true_resid = resid_ratio(ha);
+        if (!std::isfinite(S.info.true_resid)) {
+            status = QCD_ENONFINITE;
+            break;
+        }
+        if (S.info.true_resid <= tol) {
+            status = QCD_OK;
+            break;
+        }
+        if (status == QCD_ENONFINITE) break;
+        if (restart >= S.o.max_restarts || h.iter >= maxit) {
+            if (status == QCD_OK) status = QCD_ENOTCONV;
+            break;
+        }
+        // restart from the recomputed residual r = b^ - D^ x_e
+        S.info.restarts += 1;
+        TRY(state_init(c, O.st, 0.0, 0.0, maxit, BD_EPS_F64, 0));
+        TRY(set_tol2(c, O.st, S.aux, 0, 0.25 * tol * tol));
+        TRY(residual_eo(S, O.x, O.r, O.st, FIN_NONE));
+        TRY(blas_init(c, QCD_F64, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_RESTART));
+        // keep the iteration count of the cap across restarts
+        TRY(read_state(c, O.slot, &h));
+    }
+    TRY(half_to_canon(c, QCD_F64, 0, O.x, x, 0, 1, 0));
+    TRY(half_to_canon(c, QCD_F64, 0, S.xo, x, 1, 1, 0));
+    return status;
+}
+
+// Unpreconditioned FP64 BiCGStab on the full D (both parities as one vector
+// of 2*Vh_pad sites).
+int solve_full(Solver &S, const void *b, void *x, double tol)
+{
+    qcd_ctx *c = S.c;
+    const int n = 2 * c->g.Vh_pad;
+    const size_t hb = hvec_bytes(c->g, QCD_F64);
+    HVec F[8];  // b, x, r, rt, p, q, t, spare : each two halves
+    for (int k = 0; k < 8; ++k) {
+        TRY(get_work(c, QCD_F64, 2 * k, &F[k]));
+        HVec odd;
+        TRY(get_work(c, QCD_F64, 2 * k + 1, &odd));
+        if ((char *)odd.p != (char *)F[k].p + hb) {
+            set_error_message("workspace halves not contiguous");
+            return QCD_ESTATE;
+        }
+    }
+    auto half = [&](HVec v, int par) {
+        HVec h = v;
+        if (par) h.p = (char *)v.p + hb;
+        return h;
+    };
+    HVec &B = F[0], &X = F[1], &R = F[2], &RT = F[3], &P = F[4], &Q = F[5], &T = F[6];
+    SolverState *st = c->states + ST_OUTER;
+    const int *done = &st->done;
+    auto applyD = [&](HVec in, HVec out) -> int {
+        for (int par = 0; par < 2; ++par) {
+            StencilCall s;
+            s.prec = QCD_F64;
+            s.mode = M_FULL;
+            s.out_par = par;
+            s.out = half(out, par);
+            s.in = half(in, 1 - par);
+            s.y = half(in, par);
+            s.a = 1.0;
+            s.cc = -c->kappa;
+            s.done = done;
+            TRY(launch_stencil(c, s));
+        }
+        return QCD_OK;
+    };
+    TRY(canon_to_half(c, QCD_F64, 0, b, 0, half(B, 0), 1, 0));
+    TRY(canon_to_half(c, QCD_F64, 0, b, 1, half(B, 1), 1, 0));
+    S.aux = c->states + ST_AUX;
+    if (S.o.use_x0) {
+        TRY(canon_to_half(c, QCD_F64, 0, x, 0, half(X, 0), 1, 0));
+        TRY(canon_to_half(c, QCD_F64, 0, x, 1, half(X, 1), 1, 0));
+        // r = b - D x
+        for (int par = 0; par < 2; ++par) {
+            StencilCall s;
+            s.prec = QCD_F64;
+            s.mode = M_FULL;
+            s.out_par = par;
+            s.out = half(R, par);
+            s.in = half(X, 1 - par);
+            s.y = half(X, par);
+            s.a = -1.0;
+            s.cc = c->kappa;
+            s.z = half(B, par);
+            s.d = 1.0;
+            TRY(launch_stencil(c, s));
+        }
+        TRY(state_init(c, S.aux, 0.0, 0.0, 0, 0.0, 0));
+        TRY(blas_norm2(c, QCD_F64, n, B, S.aux, FIN_SETN + 0));
+        TRY(state_init(c, st, 0.0, 0.0, S.o.max_outer, BD_EPS_F64, 0));
+        TRY(set_tol2(c, st, S.aux, 0, tol * tol));
+        TRY(blas_init(c, QCD_F64, n, R, R, RT, P, X, 0, st, FIN_INIT));
+    } else {
+        TRY(state_init(c, st, 0.0, tol * tol, S.o.max_outer, BD_EPS_F64, 0));
+        TRY(blas_init(c, QCD_F64, n, B, R, RT, P, X, 1, st, FIN_INIT));
+    }
+    SolverState h;
+    int queued = 0;
+    for (;;) {
+        for (int k = 0; k < 8; ++k) {
+            TRY(applyD(P, Q));
+            TRY(blas_dot(c, QCD_F64, n, RT, Q, st, FIN_ALPHA, done));
+            TRY(blas_update_s(c, QCD_F64, n, R, Q, st));
+            TRY(applyD(R, T));
+            TRY(blas_omega(c, QCD_F64, n, T, R, st, done));
+            TRY(blas_update_x(c, QCD_F64, n, X, P, R, T, RT, st));
+            TRY(blas_update_p(c, QCD_F64, n, P, R, Q, st, FIN_NONE));
+        }
+        queued += 8;
+        TRY(read_state(c, ST_OUTER, &h));
+        if (h.done || queued > h.maxit + 16) break;
+    }
+    TRY(blas_finish_half(c, QCD_F64, n, X, P, st));
+    S.info.outer_iters = h.iter;
+    S.info.dhat_applies[QCD_F64] = 2L * h.iter - h.exit_half;
+    // true residual
+    S.aux = c->states + ST_AUX;
+    TRY(state_init(c, S.aux, 0.0, 0.0, 0, 0.0, 0));
+    TRY(blas_norm2(c, QCD_F64, n, B, S.aux, FIN_SETN + 0));
+    S.be = half(B, 0);
+    S.bo = half(B, 1);
+    S.re = half(Q, 0);
+    S.ro = half(Q, 1);
+    TRY(true_residual(S, half(X, 0), half(X, 1)));
+    SolverState ha;
+    TRY(read_state(c, ST_AUX, &ha));
+    S.info.true_resid = resid_ratio(ha);
+    TRY(half_to_canon(c, QCD_F64, 0, half(X, 0), x, 0, 1, 0));
+    TRY(half_to_canon(c, QCD_F64, 0, half(X, 1), x, 1, 1, 0));
+    int status = h.status;
+    if (!std::isfinite(S.info.true_resid)) status = QCD_ENONFINITE;
+    else if (S.info.true_resid <= tol) status = QCD_OK;
+    else if (status == QCD_OK) status = QCD_ENOTCONV;
+    return status;
+}
+
+}  // namespace
+
+int solve(qcd_ctx *c, const void *b_dev, void *x_dev, double tol, const qcd_solve_opts &o, qcd_solve_info *info)
+{
+    Solver S;
+    S.c = c;
+    S.o = o;
+    std::memset(&S.info, 0, sizeof(S.info));
+    cudaEvent_t e0, e1;
+    QCD_CUDA_CHECK(cudaEventCreate(&e0));
+    QCD_CUDA_CHECK(cudaEventCreate(&e1));
+    QCD_CUDA_CHECK(cudaEventRecord(e0, c->stream));
+    int rc = o.even_odd ? solve_eo(S, b_dev, x_dev, tol) : solve_full(S, b_dev, x_dev, tol);
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    S.info.seconds = ms * 1e-3;
+    S.info.status = rc;
+    if (info) *info = S.info;
+    return rc;
+}
+
+}  // namespace qcd

@@ -1,0 +1,156 @@
+"""GPU solves checked by the CPU oracle: every solution's true residual
+||b - D x|| / ||b|| is recomputed by the oracle in FP64 and must be <= 1e-12,
+and the solution must agree with the oracle's own solve.  Covers the
+unpreconditioned FP64 BiCGStab (4^4 workload), the even-odd FP64 BiCGStab,
+the nested FP64/FP32 scheme of Algs. 1-2, the three-level FP64/FP32/FP16
+scheme, host buffers, warm starts, and the failure paths."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1709_08785_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """4^4, links exp(i 0.3 H) seed 1, kappa 0.12, csw 1.0, antiperiodic in
+    time, Gaussian source seed 2."""
+    from paper_1709_08785_gb300 import qcd
+
+    dims, kappa, csw, t_bc = (4, 4, 4, 4), 0.12, 1.0, -1
+    U = inputs.random_gauge(dims, 0.3, 1)
+    b = inputs.gaussian_source(dims, 2)
+    F = oracle.clover_field(dims, U, kappa, csw)
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    xo, st, _ = oracle.bicgstab_full(dims, t_bc, U, F, kappa, b, 1e-13)
+    assert st == 0
+    yield dict(dims=dims, kappa=kappa, csw=csw, t_bc=t_bc, U=U, b=b, F=F, ctx=ctx, xo=xo, qcd=qcd)
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def c2s():
+    """A reduced copy of the 24^3x48 workload's parameters (eps 0.25,
+    kappa 0.124, csw 1.6) on 8^3x16, for the nested and three-level solves."""
+    from paper_1709_08785_gb300 import qcd
+
+    dims, kappa, csw, t_bc = (8, 8, 8, 16), 0.124, 1.6, -1
+    U = inputs.random_gauge(dims, 0.25, 3)
+    b = inputs.gaussian_source(dims, 4)
+    F = oracle.clover_field(dims, U, kappa, csw)
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    yield dict(dims=dims, kappa=kappa, csw=csw, t_bc=t_bc, U=U, b=b, F=F, ctx=ctx, qcd=qcd)
+    ctx.close()
+
+
+def solve(P, **kw):
+    bd = torch.from_numpy(P["b"]).cuda()
+    x = torch.zeros_like(bd)
+    info = P["ctx"].solve(bd, x, tol=kw.pop("tol", 1e-12), **kw)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), info
+
+
+def true_res(P, x):
+    return oracle.true_residual(P["dims"], P["t_bc"], P["U"], P["F"], P["kappa"], P["b"], x)
+
+
+def test_unpreconditioned_fp64(c1):
+    x, info = solve(c1, precision_levels=1, even_odd=0)
+    assert info["status"] == 0
+    assert true_res(c1, x) <= 1e-12
+    assert abs(info["true_resid"] - true_res(c1, x)) <= 1e-13
+    assert np.linalg.norm(x - c1["xo"]) / np.linalg.norm(c1["xo"]) < 1e-10
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_even_odd_solves_c1(c1, levels):
+    x, info = solve(c1, precision_levels=levels)
+    assert info["status"] == 0, info
+    assert true_res(c1, x) <= 1e-12
+    assert np.linalg.norm(x - c1["xo"]) / np.linalg.norm(c1["xo"]) < 1e-10
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_even_odd_solves_8c16(c2s, levels):
+    x, info = solve(c2s, precision_levels=levels)
+    assert info["status"] == 0, info
+    r = true_res(c2s, x)
+    assert r <= 1e-12, (r, info)
+    if levels >= 2:
+        assert info["dhat_applies"][1] > 0 and info["outer_iters"] >= 1
+    if levels == 3:
+        assert info["dhat_applies"][2] > 0
+
+
+def test_host_buffers(c1):
+    x = np.zeros_like(c1["b"])
+    info = c1["ctx"].solve(c1["b"], x, tol=1e-12, precision_levels=2)
+    assert info["status"] == 0
+    assert true_res(c1, x) <= 1e-12
+
+
+def test_warm_start_from_solution(c1):
+    bd = torch.from_numpy(c1["b"]).cuda()
+    x = torch.from_numpy(c1["xo"]).cuda()
+    info = c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, use_x0=1)
+    assert info["status"] == 0 and info["outer_iters"] <= 1
+    assert true_res(c1, x.cpu().numpy()) <= 1e-12
+
+
+def test_zero_source(c1):
+    bd = torch.zeros_like(torch.from_numpy(c1["b"])).cuda()
+    x = torch.ones_like(bd)
+    info = c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, check=False)
+    assert info["rc"] == 0
+    assert torch.count_nonzero(x).item() == 0
+
+
+def test_nonfinite_source(c1):
+    b = c1["b"].copy()
+    b[3, 1, 2] = np.nan
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    info = c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, check=False)
+    assert info["rc"] == -6  # QCD_ENONFINITE
+
+
+def test_iteration_cap(c1):
+    bd = torch.from_numpy(c1["b"]).cuda()
+    x = torch.zeros_like(bd)
+    info = c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=1, max_outer=1, max_restarts=0, check=False)
+    assert info["rc"] == -4  # QCD_ENOTCONV
+    assert info["true_resid"] > 1e-12
+
+
+def test_invalid_arguments(c1):
+    qcd = c1["qcd"]
+    bd = torch.from_numpy(c1["b"]).cuda()
+    x = torch.zeros_like(bd)
+    with pytest.raises(qcd.QCDError):
+        c1["ctx"].solve(bd, x, tol=-1.0)
+    with pytest.raises(qcd.QCDError):
+        c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, even_odd=0)
+    with pytest.raises(qcd.QCDError):
+        qcd.Context((4, 4, 3, 4))
+    ctx = qcd.Context((4, 4, 4, 4))
+    with pytest.raises(qcd.QCDError):  # no gauge field yet
+        ctx.clover_build(0.12, 1.0)
+    with pytest.raises(qcd.QCDError):
+        ctx.solve(bd, x)
+    ctx.close()
+
+
+def test_solve_repeatable_bitwise(c2s):
+    x1, i1 = solve(c2s, precision_levels=2)
+    x2, i2 = solve(c2s, precision_levels=2)
+    assert np.array_equal(x1, x2)
+    assert i1["inner_iters"] == i2["inner_iters"]
