@@ -106,6 +106,30 @@ int qcd_clover_build(qcd_ctx *ctx, double kappa, double csw);
  * The right-hand sides share every link load. */
 int qcd_dslash_eo(qcd_ctx *ctx, void *out, const void *in, int out_parity, int dagger, int prec, int nrhs);
 
+/* qcd_dslash_eo for callers that must not allocate device memory during the
+ * call (the paper has no counterpart; this is an interface convenience).
+ * qcd_dslash_eo stages its input and output through a buffer the context
+ * allocates on first use; a real-time or serving loop whose allocator must
+ * stay untouched after start-up, or a caller with a fixed memory budget or
+ * a thread that must not synchronise the device (cudaMalloc/cudaFree can),
+ * cannot take that allocation.  This variant stages through a fixed 24 MiB
+ * device array that is part of the library itself (every GPU that loads the
+ * library holds it until the process exits) and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The context (qcd_create,
+ * qcd_gauge_load) is still set up beforehand by the caller.
+ * Limits: nrhs = 1; the input and output of one half vector must fit in
+ * 24 MiB: Vh <= 65536 sites in QCD_F64 (a 16^3 x 32 lattice), more in the
+ * lower precisions; larger lattices return QCD_EINVAL.
+ * The first call on each device looks up the array's device address (with
+ * that device current), and the first call with each precision and dagger
+ * value lets the driver load the kernels it uses (with lazy module loading
+ * the driver may take device memory for their code then); make these calls
+ * during set-up, before any stream capture.  All
+ * calls share the one array: calls that overlap on the GPU (other streams,
+ * other contexts, other host threads) race; order them on one stream.
+ * Same buffer conventions and result as qcd_dslash_eo. */
+int qcd_dslash_eo_noalloc(qcd_ctx *ctx, void *out, const void *in, int out_parity, int dagger, int prec);
+
 /* out = F_pp in (inverse = 0) or F_pp^-1 in (inverse = 1) on parity p.
  * Same buffer conventions as qcd_dslash_eo.  Needs qcd_clover_build. */
 int qcd_clover_apply(qcd_ctx *ctx, void *out, const void *in, int parity, int inverse, int prec, int nrhs);

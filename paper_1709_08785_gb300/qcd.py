@@ -65,7 +65,7 @@ EXPORTS = [
     "qcd_create", "qcd_destroy", "qcd_set_stream", "qcd_gauge_load", "qcd_clover_build", "qcd_dslash_eo",
     "qcd_clover_apply", "qcd_mult_eo", "qcd_dhat", "qcd_dirac", "qcd_solve_opts_default", "qcd_solve",
     "qcd_set_profiling", "qcd_kernel_stats", "qcd_reset_kernel_stats", "qcd_strerror", "qcd_last_error",
-    "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark",
+    "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_dslash_eo_noalloc",
 ]
 
 _lib = None
@@ -113,6 +113,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.qcd_volume.restype = ctypes.c_long
     lib.qcd_launch_count.argtypes = [vp]
     lib.qcd_launch_count.restype = ctypes.c_long
+    lib.qcd_dslash_eo_noalloc.argtypes = [vp, vp, vp, ip, ip, ip]
     lib.qcd_mult_benchmark.argtypes = [vp, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
     _lib = lib
     return lib
@@ -196,6 +197,11 @@ class Context:
     # ---- operators (device buffers)
     def dslash_eo(self, out, inp, out_parity: int, dagger: bool = False, prec: int = F64, nrhs: int = 1):
         _check(self.lib.qcd_dslash_eo(self._h, _ptr(out), _ptr(inp), int(out_parity), int(dagger), int(prec), int(nrhs)))
+
+    def dslash_eo_noalloc(self, out, inp, out_parity: int, dagger: bool = False, prec: int = F64):
+        """dslash_eo that allocates no device memory during the call (staging
+        in a fixed 24 MiB array inside the library; small lattices only)."""
+        _check(self.lib.qcd_dslash_eo_noalloc(self._h, _ptr(out), _ptr(inp), int(out_parity), int(dagger), int(prec)))
 
     def mult_eo(self, out, inp, out_parity: int, dagger: bool = False, prec: int = F64, nrhs: int = 1):
         _check(self.lib.qcd_mult_eo(self._h, _ptr(out), _ptr(inp), int(out_parity), int(dagger), int(prec), int(nrhs)))
