@@ -188,6 +188,26 @@ void qcd_solve_opts_default(qcd_solve_opts *opts);
 int qcd_solve(qcd_ctx *ctx, const void *b, void *x, double tol, const qcd_solve_opts *opts,
               qcd_solve_info *info);
 
+/* lambda = D^-dag g, through gamma5-hermiticity D^dag = gamma5 D gamma5
+ * (F commutes with gamma5 and H^dag = gamma5 H gamma5, Eq. 4): lambda =
+ * gamma5 D^-1 gamma5 g, solved by qcd_solve with the same options.  g, lam:
+ * device, full-lattice complex128 [V][4][3].  Used by the backward pass of a
+ * solve: for x = D^-1 b and a real loss with gradient g with respect to x,
+ * the gradient with respect to b is lambda.  Returns qcd_solve's status. */
+int qcd_solve_adjoint(qcd_ctx *ctx, const void *g, void *lam, double tol, const qcd_solve_opts *opts,
+                      qcd_solve_info *info);
+
+/* Link gradient ("force"): G = df/dRe U + i df/dIm U of
+ * f(U) = -Re <lam, D[U] x> with x and lam held fixed -- for x = D^-1 b and
+ * lam = D^-dag g this is the gradient of a real loss with respect to the
+ * links (the convention torch uses for complex tensors).  Both the hopping
+ * term (Eq. 4; outer products of lam and the spin-projected x across each
+ * link) and the clover term (the plaquette leaves with the spin-traced
+ * insertion Tr_spin[sigma_munu x lam^dag] at each corner) contribute.
+ * U: the device gauge field in canonical layout (the one loaded); x, lam:
+ * device complex128 [V][4][3]; G: device complex128 [V][4][3][3]. FP64. */
+int qcd_force(qcd_ctx *ctx, const void *U, const void *x, const void *lam, void *G);
+
 /* Kernel timing: when enabled, each launch of the fused MULT kernel
  * (and of the other solver kernels) is bracketed by CUDA events on the
  * context stream; qcd_kernel_stats sums them. */

@@ -530,6 +530,50 @@ extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const q
     return rc;
 }
 
+// ---------------------------------------------------------------- adjoint
+extern "C" int qcd_solve_adjoint(qcd_ctx *c, const void *g, void *lam, double tol, const qcd_solve_opts *opts,
+                                 qcd_solve_info *info)
+{
+    if (!c || !g || !lam) {
+        set_error_message("null argument");
+        return QCD_EINVAL;
+    }
+    if (!is_device_ptr(g) || !is_device_ptr(lam)) {
+        set_error_message("qcd_solve_adjoint takes device buffers");
+        return QCD_EINVAL;
+    }
+    if (!c->have_clover) {
+        set_error_message("qcd_solve_adjoint needs qcd_gauge_load and qcd_clover_build first");
+        return QCD_ESTATE;
+    }
+    int rc;
+    if (!c->adj_buf && (rc = dev_alloc(c, &c->adj_buf, (size_t)c->g.V * 12 * 16))) return rc;
+    // D^-dag = gamma5 D^-1 gamma5
+    if ((rc = gamma5_full(c, g, c->adj_buf))) return rc;
+    const int src = qcd_solve(c, c->adj_buf, lam, tol, opts, info);
+    if (src != QCD_OK && src != QCD_ENOTCONV && src != QCD_EBREAKDOWN) return src;
+    if ((rc = gamma5_full(c, lam, lam))) return rc;
+    QCD_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    return src;
+}
+
+extern "C" int qcd_force(qcd_ctx *c, const void *U, const void *x, const void *lam, void *G)
+{
+    if (!c || !U || !x || !lam || !G) {
+        set_error_message("null argument");
+        return QCD_EINVAL;
+    }
+    if (!is_device_ptr(U) || !is_device_ptr(x) || !is_device_ptr(lam) || !is_device_ptr(G)) {
+        set_error_message("qcd_force takes device buffers");
+        return QCD_EINVAL;
+    }
+    if (!c->have_clover) {
+        set_error_message("qcd_force needs kappa and csw from qcd_clover_build");
+        return QCD_ESTATE;
+    }
+    return force(c, x, lam, G, U);
+}
+
 // ---------------------------------------------------------------- profiling
 extern "C" int qcd_set_profiling(qcd_ctx *c, int on)
 {

@@ -115,6 +115,11 @@ struct qcd_ctx {
     void *bench_buf = nullptr;
     size_t bench_bytes = 0;
     void *flush_buf = nullptr;
+
+    // force: the per-site insertion matrices; adjoint solve: gamma5 g
+    void *force_buf = nullptr;
+    size_t force_bytes = 0;
+    void *adj_buf = nullptr;
 };
 
 namespace qcd {
@@ -171,5 +176,9 @@ int clover_apply_half(qcd_ctx *c, int prec, int parity, int inverse, HVec in, HV
 
 // solver.cu
 int solve(qcd_ctx *c, const void *b_dev, void *x_dev, double tol, const qcd_solve_opts &o, qcd_solve_info *info);
+
+// force.cu
+int force(qcd_ctx *c, const void *x, const void *lam, void *G, const void *U_canon);
+int gamma5_full(qcd_ctx *c, const void *in, void *out);
 
 }  // namespace qcd

@@ -65,7 +65,8 @@ EXPORTS = [
     "qcd_create", "qcd_destroy", "qcd_set_stream", "qcd_gauge_load", "qcd_clover_build", "qcd_dslash_eo",
     "qcd_clover_apply", "qcd_mult_eo", "qcd_dhat", "qcd_dirac", "qcd_solve_opts_default", "qcd_solve",
     "qcd_set_profiling", "qcd_kernel_stats", "qcd_reset_kernel_stats", "qcd_strerror", "qcd_last_error",
-    "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_dslash_eo_noalloc",
+    "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_dslash_eo_noalloc", "qcd_solve_adjoint",
+    "qcd_force",
 ]
 
 _lib = None
@@ -115,6 +116,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.qcd_launch_count.restype = ctypes.c_long
     lib.qcd_dslash_eo_noalloc.argtypes = [vp, vp, vp, ip, ip, ip]
     lib.qcd_mult_benchmark.argtypes = [vp, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
+    lib.qcd_solve_adjoint.argtypes = [vp, vp, vp, dp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
+    lib.qcd_force.argtypes = [vp, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -226,6 +229,24 @@ class Context:
         d = info.as_dict()
         d["rc"] = rc
         return d
+
+    def solve_adjoint(self, g, lam, tol: float = 1e-12, opts: SolveOpts | None = None, check: bool = True,
+                      **kw) -> dict:
+        """lam = D^-dag g (device buffers)."""
+        if opts is None:
+            opts = default_opts(**kw)
+        info = SolveInfo()
+        rc = self.lib.qcd_solve_adjoint(self._h, _ptr(g), _ptr(lam), float(tol), ctypes.byref(opts),
+                                        ctypes.byref(info))
+        if check:
+            _check(rc)
+        d = info.as_dict()
+        d["rc"] = rc
+        return d
+
+    def force(self, U, x, lam, G):
+        """G = gradient of -Re<lam, D[U] x> with respect to the links (device buffers)."""
+        _check(self.lib.qcd_force(self._h, _ptr(U), _ptr(x), _ptr(lam), _ptr(G)))
 
     # ---- kernel timing
     def set_profiling(self, on: bool):
