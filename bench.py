@@ -40,6 +40,7 @@ WORKLOAD_NAME = ("24^3x48 clover-Wilson, even-odd preconditioned nested BiCGStab
 # MULT (in 96 + links 8x48 + clover 288 + out 96) and the fused second half
 STENCIL_SOURCES = ["paper_1709_08785_gb300/csrc/stencil.cu", "paper_1709_08785_gb300/csrc/qcd_internal.cuh",
                    "paper_1709_08785_gb300/csrc/reduce.cuh"]
+TUNE_CACHE = os.path.join(ROOT, "paper_1709_08785_gb300", "_build", "tune_cache.json")
 
 
 def peaks():
@@ -199,6 +200,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     setup_ms = e0.elapsed_time(e1)
     del Ud
+    ctx.autotune(TUNE_CACHE)
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bd)
     opts = qcd.default_opts(precision_levels=2, inner_tol=[W["inner_tol"], 1e-2])
@@ -369,6 +371,7 @@ def run_dslash_only(args):
     ctx = qcd.Context(dims, W["t_bc"], torch.cuda.current_stream())
     ctx.gauge_load(torch.from_numpy(U).cuda())
     ctx.clover_build(W["kappa"], W["csw"])
+    ctx.autotune(TUNE_CACHE)
     hbm, kind = peaks()
     out = {"mode": "dslash-only", "lattice": list(dims), "peak_gbs": hbm, "peak_kind": kind}
     for name, p, nrhs in (("f32", qcd.F32, 1), ("f16", qcd.F16, 1), ("f64", qcd.F64, 1), ("f32_12rhs", qcd.F32, 12)):

@@ -188,6 +188,36 @@ void qcd_solve_opts_default(qcd_solve_opts *opts);
 int qcd_solve(qcd_ctx *ctx, const void *b, void *x, double tol, const qcd_solve_opts *opts,
               qcd_solve_info *info);
 
+/* Batched solves: n independent problems, problem i solving D_i x_i = b_i on
+ * the lattice, gauge field and clover term of context ctxs[i] (distinct
+ * contexts on one device; their lattices may differ), each to
+ * ||b_i - D_i x_i|| / ||b_i|| <= tol[i].  The nested FP64/FP32 scheme of
+ * Algs. 1-2 runs for all problems at once: every outer half-step is one
+ * persistent cooperative kernel whose phases (the whole inner FP32
+ * iteration, then the FP64 D^ and update) walk work tiles across all
+ * lattices, with per-problem scalars and exit flags in device memory; the
+ * two half-steps of an outer iteration are captured in a CUDA graph and
+ * replayed until every problem has converged.  A problem whose true
+ * residual misses its tolerance is restarted alone from its iterate.
+ * b[i], x[i]: device, full-lattice complex128 [V_i][4][3].  opts: NULL or
+ * precision_levels = 2, even_odd = 1, use_x0 = 0 (inner_tol[0], max_outer,
+ * max_inner[0] are used).  infos: NULL or n entries (seconds = the whole
+ * batch).  Work is ordered on ctxs[0]'s stream; synchronous.
+ * Errors: QCD_ETIMEOUT if a grid barrier gave up (see qcd_set_wait_limit);
+ * the first failing problem's status otherwise. */
+int qcd_solve_batched(qcd_ctx *const *ctxs, int n, const void *const *b, void *const *x, const double *tol,
+                      const qcd_solve_opts *opts, qcd_solve_info *infos);
+
+/* Every device-side wait of the library (the grid barriers of the batched
+ * kernel) spins at most this many times (about 100 ns each) before it
+ * records QCD_ETIMEOUT and the kernel returns; default 1e7 (about a second).
+ * Process-wide. */
+int qcd_set_wait_limit(long long spins);
+
+/* Use CUDA graphs for the batched solver's replayed launches (1, default) or
+ * launch directly (0).  Process-wide. */
+int qcd_set_graphs(int on);
+
 /* lambda = D^-dag g, through gamma5-hermiticity D^dag = gamma5 D gamma5
  * (F commutes with gamma5 and H^dag = gamma5 H gamma5, Eq. 4): lambda =
  * gamma5 D^-1 gamma5 g, solved by qcd_solve with the same options.  g, lam:
@@ -232,6 +262,21 @@ int qcd_reset_kernel_stats(qcd_ctx *ctx);
 
 /* Number of kernels this context has launched since it was created. */
 long qcd_launch_count(const qcd_ctx *ctx);
+
+/* Autotune the launch configurations of the operator kernels the solvers
+ * use (register budget and threads per block, for each precision, fused
+ * reduction and right-hand-side count): every candidate is timed on scratch
+ * buffers, with L2 evicted, and the fastest kept for this context.  If
+ * cache_path is not NULL the choices are read from and added to that JSON
+ * file, keyed by device name, lattice extents and configuration, so a later
+ * context tunes nothing it finds there.  Needs qcd_clover_build.
+ * Synchronous. */
+int qcd_autotune(qcd_ctx *ctx, const char *cache_path);
+
+/* The tuned configurations: up to max entries (key, variant 0/1, threads per
+ * block along the sites, microseconds per launch); returns the number of
+ * entries held. Any output pointer may be NULL. */
+int qcd_tune_info(qcd_ctx *ctx, int max, unsigned *keys, int *variant, int *threads, double *us);
 
 /* Time the fused MULT kernel (Sec. II-B, out = F^-1 H_{p,1-p} in) alone on
  * internal, already-resident buffers: `iters` launches on nrhs right-hand

@@ -530,6 +530,69 @@ extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const q
     return rc;
 }
 
+// ---------------------------------------------------------------- batched
+static long long g_wait_limit = 10000000LL;  // ~1 s of bounded spinning per device wait
+static int g_use_graphs = 1;
+
+extern "C" int qcd_set_wait_limit(long long spins)
+{
+    if (spins < 1) return QCD_EINVAL;
+    g_wait_limit = spins;
+    return QCD_OK;
+}
+
+extern "C" int qcd_set_graphs(int on)
+{
+    g_use_graphs = on ? 1 : 0;
+    return QCD_OK;
+}
+
+extern "C" int qcd_solve_batched(qcd_ctx *const *ctxs, int n, const void *const *b, void *const *x,
+                                 const double *tol, const qcd_solve_opts *opts, qcd_solve_info *infos)
+{
+    if (!ctxs || n < 1 || !b || !x || !tol) {
+        set_error_message("null argument or empty batch");
+        return QCD_EINVAL;
+    }
+    qcd_solve_opts o;
+    qcd_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision_levels != 2 || !o.even_odd || o.use_x0 || o.max_outer < 1 || o.max_inner[0] < 1 ||
+        !(o.inner_tol[0] > 0.0)) {
+        set_error_message("batched solves run the even-odd FP64/FP32 scheme from x = 0");
+        return QCD_EINVAL;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !b[i] || !x[i] || !(tol[i] > 0.0)) {
+            set_error_message("problem %d: null argument or bad tolerance", i);
+            return QCD_EINVAL;
+        }
+        if (!is_device_ptr(b[i]) || !is_device_ptr(x[i])) {
+            set_error_message("problem %d: qcd_solve_batched takes device buffers", i);
+            return QCD_EINVAL;
+        }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) {
+                set_error_message("problems %d and %d share a context", j, i);
+                return QCD_EINVAL;
+            }
+    }
+    cudaEvent_t e0, e1;
+    QCD_CUDA_CHECK(cudaEventCreate(&e0));
+    QCD_CUDA_CHECK(cudaEventCreate(&e1));
+    QCD_CUDA_CHECK(cudaEventRecord(e0, ctxs[0]->stream));
+    const int rc = batched_solve((qcd_ctx **)ctxs, n, b, x, tol, o, infos, g_wait_limit, g_use_graphs);
+    cudaEventRecord(e1, ctxs[0]->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (infos)
+        for (int i = 0; i < n; ++i) infos[i].seconds = ms * 1e-3;
+    return rc;
+}
+
 // ---------------------------------------------------------------- adjoint
 extern "C" int qcd_solve_adjoint(qcd_ctx *c, const void *g, void *lam, double tol, const qcd_solve_opts *opts,
                                  qcd_solve_info *info)
@@ -605,6 +668,18 @@ extern "C" int qcd_reset_kernel_stats(qcd_ctx *c)
 }
 
 extern "C" long qcd_launch_count(const qcd_ctx *c) { return c ? c->launches : 0; }
+
+extern "C" int qcd_autotune(qcd_ctx *c, const char *cache_path)
+{
+    if (!c) return QCD_EINVAL;
+    return autotune(c, cache_path);
+}
+
+extern "C" int qcd_tune_info(qcd_ctx *c, int max, unsigned *keys, int *variant, int *threads, double *us)
+{
+    if (!c || max < 0) return QCD_EINVAL;
+    return tune_entries(c, max, keys, variant, threads, us);
+}
 
 extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, double *ms_per_launch,
                                   double *bytes_per_launch)

@@ -8,80 +8,9 @@
 // marked done, so a host can queue iterations ahead without reading
 // anything back.
 #include "blas.cuh"
-#include "reduce.cuh"
+#include "blas_ops.cuh"
 
 namespace qcd {
-
-// ---------------------------------------------------------------- helpers
-template <class T>
-__device__ __forceinline__ double norm2_sp(const Spinor<T> &a)
-{
-    T s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) s += a.s[k][i].r * a.s[k][i].r + a.s[k][i].i * a.s[k][i].i;
-    return (double)s;
-}
-
-// <a|b> = sum conj(a) b
-template <class T>
-__device__ __forceinline__ void dot_sp(const Spinor<T> &a, const Spinor<T> &b, double &re, double &im)
-{
-    T r = 0, i = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            r += a.s[k][c].r * b.s[k][c].r + a.s[k][c].i * b.s[k][c].i;
-            i += a.s[k][c].r * b.s[k][c].i - a.s[k][c].i * b.s[k][c].r;
-        }
-    re += (double)r;
-    im += (double)i;
-}
-
-// y += a x (complex a)
-template <class T>
-__device__ __forceinline__ void caxpy(Spinor<T> &y, cx<T> a, const Spinor<T> &x)
-{
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) fma_(y.s[k][c], a, x.s[k][c]);
-}
-
-template <class T>
-__device__ __forceinline__ cx<T> scal(const double *v, double sgn = 1.0)
-{
-    return mk(T(sgn * v[0]), T(sgn * v[1]));
-}
-
-template <class T>
-__device__ __forceinline__ void zero_sp(Spinor<T> &a)
-{
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) a.s[k][c] = mk(T(0), T(0));
-}
-
-template <class T>
-__device__ __forceinline__ void scale_sp(Spinor<T> &a, T s)
-{
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) a.s[k][c] = mk(a.s[k][c].r * s, a.s[k][c].i * s);
-}
-
-template <class TO, class TI>
-__device__ __forceinline__ void cvt_sp(Spinor<TO> &o, const Spinor<TI> &a)
-{
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o.s[k][c] = mk((TO)a.s[k][c].r, (TO)a.s[k][c].i);
-}
 
 // Grid-stride driver: each thread applies op to its sites, reduces NRED
 // doubles over the grid and runs the finaliser.
@@ -119,240 +48,6 @@ static int run(qcd_ctx *c, int nsites, const Op &op, int fin, SolverState *st, c
 }
 
 static double sp_bytes(int prec) { return prec == QCD_F64 ? 192.0 : prec == QCD_F32 ? 96.0 : 52.0; }
-
-// ---------------------------------------------------------------- BiCGStab updates
-// s = r - alpha q (r overwritten), |s|^2
-template <int P>
-struct OpS {
-    SpinorPtr r, q;
-    const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> R, Q;
-        Prec<P>::load(r, cb, R);
-        Prec<P>::load(q, cb, Q);
-        caxpy(R, scal<T>(st->alpha, -1.0), Q);
-        Prec<P>::store(r, cb, R);
-        acc[0] += norm2_sp(R);
-    }
-};
-
-// x += alpha p + omega s; r = s - omega t; |r|^2, <r~|r>
-template <int P>
-struct OpX {
-    SpinorPtr x, p, r, t, rt;
-    const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> X, Pp, R, Tt, Rt;
-        Prec<P>::load(x, cb, X);
-        Prec<P>::load(p, cb, Pp);
-        Prec<P>::load(r, cb, R);
-        caxpy(X, scal<T>(st->alpha), Pp);
-        caxpy(X, scal<T>(st->omega), R);
-        Prec<P>::store(x, cb, X);
-        Prec<P>::load(t, cb, Tt);
-        caxpy(R, scal<T>(st->omega, -1.0), Tt);
-        Prec<P>::store(r, cb, R);
-        Prec<P>::load(rt, cb, Rt);
-        acc[0] += norm2_sp(R);
-        dot_sp(Rt, R, acc[1], acc[2]);
-    }
-};
-
-// p = r + beta (p - omega q), |p|^2
-template <int P>
-struct OpP {
-    SpinorPtr p, r, q;
-    const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> Pp, R, Q;
-        Prec<P>::load(p, cb, Pp);
-        Prec<P>::load(q, cb, Q);
-        caxpy(Pp, scal<T>(st->omega, -1.0), Q);
-        Prec<P>::load(r, cb, R);
-        const cx<T> b = scal<T>(st->beta);
-        Spinor<T> O = R;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) fma_(O.s[k][c], b, Pp.s[k][c]);
-        Prec<P>::store(p, cb, O);
-        acc[0] += norm2_sp(O);
-    }
-};
-
-// x += alpha p when the iteration stopped after its first half-step
-template <int P>
-struct OpHalf {
-    SpinorPtr x, p;
-    const SolverState *st;
-    __device__ void operator()(int cb, double *) const
-    {
-        using T = typename Prec<P>::T;
-        if (!st->exit_half) return;
-        Spinor<T> X, Pp;
-        Prec<P>::load(x, cb, X);
-        Prec<P>::load(p, cb, Pp);
-        caxpy(X, scal<T>(st->alpha), Pp);
-        Prec<P>::store(x, cb, X);
-    }
-};
-
-// flexible (Alg. 1) updates: x += alpha v; r -= alpha q; |r|^2
-template <int P>
-struct OpFlex1 {
-    SpinorPtr x, v, r, q;
-    const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> X, V, R, Q;
-        Prec<P>::load(x, cb, X);
-        Prec<P>::load(v, cb, V);
-        caxpy(X, scal<T>(st->alpha), V);
-        Prec<P>::store(x, cb, X);
-        Prec<P>::load(r, cb, R);
-        Prec<P>::load(q, cb, Q);
-        caxpy(R, scal<T>(st->alpha, -1.0), Q);
-        Prec<P>::store(r, cb, R);
-        acc[0] += norm2_sp(R);
-    }
-};
-
-// x += omega v; r -= omega t; |r|^2, <r~|r>
-template <int P>
-struct OpFlex2 {
-    SpinorPtr x, v, r, t, rt;
-    const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> X, V, R, Tt, Rt;
-        Prec<P>::load(x, cb, X);
-        Prec<P>::load(v, cb, V);
-        caxpy(X, scal<T>(st->omega), V);
-        Prec<P>::store(x, cb, X);
-        Prec<P>::load(r, cb, R);
-        Prec<P>::load(t, cb, Tt);
-        caxpy(R, scal<T>(st->omega, -1.0), Tt);
-        Prec<P>::store(r, cb, R);
-        Prec<P>::load(rt, cb, Rt);
-        acc[0] += norm2_sp(R);
-        dot_sp(Rt, R, acc[1], acc[2]);
-    }
-};
-
-// r = r~ = p = src (optionally x = 0), |r|^2
-template <int P>
-struct OpInit {
-    SpinorPtr src, r, rt, p, x;
-    int zero_x;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> S;
-        Prec<P>::load(src, cb, S);
-        if (r.p != src.p) Prec<P>::store(r, cb, S);
-        Prec<P>::store(rt, cb, S);
-        Prec<P>::store(p, cb, S);
-        if (zero_x) {
-            Spinor<T> Z;
-            zero_sp(Z);
-            Prec<P>::store(x, cb, Z);
-        }
-        acc[0] += norm2_sp(S);
-    }
-};
-
-// lower-precision start of an inner solve (Alg. 2): b = src/|src|,
-// r = r~ = p = b, x = 0
-template <int PS, int PD>
-struct OpInner {
-    SpinorPtr src, r, rt, p, x;
-    const double *src_norm2;
-    __device__ void operator()(int cb, double *) const
-    {
-        using TS = typename Prec<PS>::T;
-        using TD = typename Prec<PD>::T;
-        Spinor<TS> S;
-        Prec<PS>::load(src, cb, S);
-        const double n2 = *src_norm2;
-        const TS inv = n2 > 0.0 ? TS(1.0 / sqrt(n2)) : TS(0);
-        scale_sp(S, inv);
-        Spinor<TD> D;
-        cvt_sp(D, S);
-        Prec<PD>::store(r, cb, D);
-        Prec<PD>::store(rt, cb, D);
-        Prec<PD>::store(p, cb, D);
-        Spinor<TD> Z;
-        zero_sp(Z);
-        Prec<PD>::store(x, cb, Z);
-    }
-};
-
-// v (higher precision) = |src| * x (lower precision), Alg. 2's last step
-template <int PS, int PD>
-struct OpLift {
-    SpinorPtr x, v;
-    const double *src_norm2;
-    __device__ void operator()(int cb, double *) const
-    {
-        using TS = typename Prec<PS>::T;
-        using TD = typename Prec<PD>::T;
-        Spinor<TS> X;
-        Prec<PS>::load(x, cb, X);
-        Spinor<TD> V;
-        cvt_sp(V, X);
-        scale_sp(V, TD(sqrt(*src_norm2)));
-        Prec<PD>::store(v, cb, V);
-    }
-};
-
-template <int P>
-struct OpNorm {
-    SpinorPtr a;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> A;
-        Prec<P>::load(a, cb, A);
-        acc[0] += norm2_sp(A);
-    }
-};
-
-// <a|b>
-template <int P>
-struct OpDot {
-    SpinorPtr a, b;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> A, B;
-        Prec<P>::load(a, cb, A);
-        Prec<P>::load(b, cb, B);
-        dot_sp(A, B, acc[0], acc[1]);
-    }
-};
-
-// <t|r>, |t|^2
-template <int P>
-struct OpOmega {
-    SpinorPtr t, r;
-    __device__ void operator()(int cb, double *acc) const
-    {
-        using T = typename Prec<P>::T;
-        Spinor<T> A, B;
-        Prec<P>::load(t, cb, A);
-        Prec<P>::load(r, cb, B);
-        dot_sp(A, B, acc[0], acc[1]);
-        acc[2] += norm2_sp(A);
-    }
-};
 
 // ---------------------------------------------------------------- state
 __global__ void k_state_init(SolverState *st, double tol2, double tol2_rel, int maxit, double bd_eps, int unit)

@@ -3,6 +3,7 @@
 // single-pass grid reduction, and the kernel launchers.
 #pragma once
 
+#include <unordered_map>
 #include <vector>
 
 #include "qcd_internal.cuh"
@@ -120,13 +121,27 @@ struct qcd_ctx {
     void *force_buf = nullptr;
     size_t force_bytes = 0;
     void *adj_buf = nullptr;
+
+    // autotuned launch configurations of the stencil kernels, by tune_key
+    struct TuneEntry {
+        int variant;  // 0: compiler's register budget, 1: capped at 80
+        int bx;       // threads per block along the sites
+        double us;    // measured time of one launch
+    };
+    std::unordered_map<unsigned, TuneEntry> tune;
+    void *tune_buf = nullptr;
+    size_t tune_bytes = 0;
+
+    // batched solves led by this context: problem descriptors, barrier words
+    void *batch_buf = nullptr;
+    size_t batch_bytes = 0;
 };
 
 namespace qcd {
 
 constexpr int NSTATES = 8;
 constexpr int PROF_CAP = 1 << 16;  // profiled launches between two collections
-enum StateSlot { ST_OUTER = 0, ST_MID = 1, ST_INNER = 2, ST_AUX = 3 };
+enum StateSlot { ST_OUTER = 0, ST_MID = 1, ST_INNER = 2, ST_AUX = 3, ST_TUNE = 4 };
 
 // allocation helpers (api.cu)
 int dev_alloc(qcd_ctx *c, void **p, size_t bytes);
@@ -164,8 +179,11 @@ struct StencilCall {
     size_t norm_stride = 0;
     RedArgs red_args;
     const int *done = nullptr;
+    int force_variant = -1;  // >= 0: bypass the tuned configuration (autotuner)
+    int force_bx = 128;
 };
 int launch_stencil(qcd_ctx *c, const StencilCall &s);
+unsigned tune_key(const StencilCall &s);
 double stencil_bytes(const qcd_ctx *c, const StencilCall &s);  // algorithmic bytes of one launch
 int fill_pattern(qcd_ctx *c, int prec, HVec v, int nrhs, size_t rhs_stride, int seed);
 
@@ -176,6 +194,14 @@ int clover_apply_half(qcd_ctx *c, int prec, int parity, int inverse, HVec in, HV
 
 // solver.cu
 int solve(qcd_ctx *c, const void *b_dev, void *x_dev, double tol, const qcd_solve_opts &o, qcd_solve_info *info);
+
+// batched.cu
+int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, const double *tol,
+                  const qcd_solve_opts &o, qcd_solve_info *infos, long long spin_limit, int use_graph);
+
+// tune.cu
+int autotune(qcd_ctx *c, const char *cache_path);
+int tune_entries(qcd_ctx *c, int max, unsigned *keys, int *variant, int *bx, double *us);
 
 // force.cu
 int force(qcd_ctx *c, const void *x, const void *lam, void *G, const void *U_canon);

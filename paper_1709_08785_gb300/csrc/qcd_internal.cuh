@@ -351,6 +351,40 @@ struct Prec<QCD_F16> {
     }
 };
 
+// Coherent variants (P + COHERENT): spinor loads bypass L1 and the
+// read-only path (ld.global.cg), for kernels that read vectors other blocks
+// wrote earlier in the same launch (the persistent batched solver, whose
+// phases are separated by grid barriers).  Links and clover entries never
+// change inside a launch and keep the read-only path.
+constexpr int COHERENT = 16;
+
+template <>
+struct Prec<QCD_F64 + COHERENT> : Prec<QCD_F64> {
+    static __device__ __forceinline__ void load(const SpinorPtr &v, int cb, Spinor<T> &s)
+    {
+        const double2 *p = (const double2 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 d = __ldcg(p + soa(cb, 12, k));
+            s.s[k / 3][k % 3] = mk(d.x, d.y);
+        }
+    }
+};
+
+template <>
+struct Prec<QCD_F32 + COHERENT> : Prec<QCD_F32> {
+    static __device__ __forceinline__ void load(const SpinorPtr &v, int cb, Spinor<T> &s)
+    {
+        const float4 *p = (const float4 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float4 f = __ldcg(p + soa(cb, 6, k));
+            s.s[(2 * k) / 3][(2 * k) % 3] = mk(f.x, f.y);
+            s.s[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(f.z, f.w);
+        }
+    }
+};
+
 // ---------------------------------------------------------------- clover
 // y = A x for a 6x6 Hermitian block (d real diagonal, o lower triangle,
 // row-major: o[0]=(1,0), o[1]=(2,0), o[2]=(2,1), o[3]=(3,0), ...).

@@ -1,0 +1,181 @@
+// Device pieces of the hopping stencil (Eq. 4) shared by the stencil
+// kernels and the batched persistent solver: spin projection before the
+// colour multiply, 12-real link reconstruction through Prec<P>, and the
+// 8-direction accumulation.
+#pragma once
+
+#include "reduce.cuh"
+
+namespace qcd {
+
+// ---- spin projection in the Dirac basis --------------------------------
+// S = +1: projector (1 - gamma_mu);  S = -1: (1 + gamma_mu).
+// For mu = x, y, z: (1 - S g_k) psi = (h, -S i s_k h) with
+// h = psi_up + S i s_k psi_dn.  For mu = t: (1 - S g_t) keeps the lower
+// (S = +1) or upper (S = -1) pair, times 2.
+template <int MU, int S, class T>
+__device__ __forceinline__ void project(const Spinor<T> &p, cx<T> h[2][3])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (MU == 0) {  // i s_1 psi_dn = (i psi3, i psi2)
+            h[0][i] = S > 0 ? p.s[0][i] + ti(p.s[3][i]) : p.s[0][i] - ti(p.s[3][i]);
+            h[1][i] = S > 0 ? p.s[1][i] + ti(p.s[2][i]) : p.s[1][i] - ti(p.s[2][i]);
+        } else if (MU == 1) {  // i s_2 psi_dn = (psi3, -psi2)
+            h[0][i] = S > 0 ? p.s[0][i] + p.s[3][i] : p.s[0][i] - p.s[3][i];
+            h[1][i] = S > 0 ? p.s[1][i] - p.s[2][i] : p.s[1][i] + p.s[2][i];
+        } else if (MU == 2) {  // i s_3 psi_dn = (i psi2, -i psi3)
+            h[0][i] = S > 0 ? p.s[0][i] + ti(p.s[2][i]) : p.s[0][i] - ti(p.s[2][i]);
+            h[1][i] = S > 0 ? p.s[1][i] - ti(p.s[3][i]) : p.s[1][i] + ti(p.s[3][i]);
+        } else {
+            const T two = T(2);
+            h[0][i] = S > 0 ? two * p.s[2][i] : two * p.s[0][i];
+            h[1][i] = S > 0 ? two * p.s[3][i] : two * p.s[1][i];
+        }
+    }
+}
+
+// acc += expansion of the projected, colour-multiplied pair g
+template <int MU, int S, class T>
+__device__ __forceinline__ void expand(Spinor<T> &acc, const cx<T> g[2][3])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (MU == 3) {
+            if (S > 0) {
+                acc.s[2][i] = acc.s[2][i] + g[0][i];
+                acc.s[3][i] = acc.s[3][i] + g[1][i];
+            } else {
+                acc.s[0][i] = acc.s[0][i] + g[0][i];
+                acc.s[1][i] = acc.s[1][i] + g[1][i];
+            }
+        } else {
+            acc.s[0][i] = acc.s[0][i] + g[0][i];
+            acc.s[1][i] = acc.s[1][i] + g[1][i];
+            if (MU == 0) {  // lower = -S i (g1, g0)
+                acc.s[2][i] = S > 0 ? acc.s[2][i] - ti(g[1][i]) : acc.s[2][i] + ti(g[1][i]);
+                acc.s[3][i] = S > 0 ? acc.s[3][i] - ti(g[0][i]) : acc.s[3][i] + ti(g[0][i]);
+            } else if (MU == 1) {  // lower = -S (g1, -g0)
+                acc.s[2][i] = S > 0 ? acc.s[2][i] - g[1][i] : acc.s[2][i] + g[1][i];
+                acc.s[3][i] = S > 0 ? acc.s[3][i] + g[0][i] : acc.s[3][i] - g[0][i];
+            } else {  // lower = -S i (g0, -g1)
+                acc.s[2][i] = S > 0 ? acc.s[2][i] - ti(g[0][i]) : acc.s[2][i] + ti(g[0][i]);
+                acc.s[3][i] = S > 0 ? acc.s[3][i] + ti(g[1][i]) : acc.s[3][i] - ti(g[1][i]);
+            }
+        }
+    }
+}
+
+// g = U h  or  g = U^dag h, for both spin rows
+template <bool DAG, class T>
+__device__ __forceinline__ void colour_mul(const Link<T> &U, const cx<T> h[2][3], cx<T> g[2][3])
+{
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            cx<T> s = mk(T(0), T(0));
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (DAG) fmac_(s, U.u[j][i], h[a][j]);
+                else fma_(s, U.u[i][j], h[a][j]);
+            }
+            g[a][i] = s;
+        }
+}
+
+template <int P, int MU, int SF>
+__device__ __forceinline__ void hop_dir(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par, int cb,
+                                        int lex, const int c[4], Spinor<typename Prec<P>::T> &acc)
+{
+    using T = typename Prec<P>::T;
+    const int in_par = 1 - out_par;
+    {  // forward hop: (1 - SF g_mu) U_mu(n) psi(n + mu)
+        const int nb = lex_hop(g, lex, c, MU, +1) >> 1;
+        Spinor<T> psi;
+        Prec<P>::load(in, nb, psi);
+        cx<T> h[2][3], q[2][3];
+        project<MU, SF>(psi, h);
+        Link<T> L;
+        Prec<P>::load_link(U, out_par, cb, MU, L);
+        colour_mul<false>(L, h, q);
+        if (MU == 3 && g.t_bc < 0 && c[3] == g.L[3] - 1) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) q[a][i] = -q[a][i];
+        }
+        expand<MU, SF>(acc, q);
+    }
+    {  // backward hop: (1 + SF g_mu) U_mu(n - mu)^dag psi(n - mu)
+        const int nb = lex_hop(g, lex, c, MU, -1) >> 1;
+        Spinor<T> psi;
+        Prec<P>::load(in, nb, psi);
+        cx<T> h[2][3], q[2][3];
+        project<MU, -SF>(psi, h);
+        Link<T> L;
+        Prec<P>::load_link(U, in_par, nb, MU, L);
+        colour_mul<true>(L, h, q);
+        if (MU == 3 && g.t_bc < 0 && c[3] == 0) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) q[a][i] = -q[a][i];
+        }
+        expand<MU, -SF>(acc, q);
+    }
+}
+
+// acc = H in at site cb of parity out_par (DAG: gamma5 H gamma5, i.e. the
+// projector signs exchanged)
+template <int P, bool DAG>
+__device__ __forceinline__ void hopping(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par, int cb,
+                                        Spinor<typename Prec<P>::T> &acc)
+{
+    using T = typename Prec<P>::T;
+    int c[4];
+    site_coords(g, out_par, cb, c);
+    const int lex = lex_of(g, c);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc.s[a][i] = mk(T(0), T(0));
+    constexpr int SF = DAG ? -1 : 1;
+    hop_dir<P, 0, SF>(g, U, in, out_par, cb, lex, c, acc);
+    hop_dir<P, 1, SF>(g, U, in, out_par, cb, lex, c, acc);
+    hop_dir<P, 2, SF>(g, U, in, out_par, cb, lex, c, acc);
+    hop_dir<P, 3, SF>(g, U, in, out_par, cb, lex, c, acc);
+}
+
+struct StencilArgs {
+    Geom g;
+    GaugePtr U;
+    CloverPtr C;
+    SpinorPtr out, in, y, aux, z;
+    int out_par;
+    double a, cc, d;
+    size_t rhs_stride;   // in 16-byte elements
+    size_t norm_stride;  // in floats
+    RedArgs red;
+    const int *done;
+    int *skip;  // profiling: set to 1 when the launch returns early
+};
+
+__device__ __forceinline__ SpinorPtr rhs_ptr(const SpinorPtr &v, int r, size_t stride, size_t nstride)
+{
+    SpinorPtr o;
+    o.p = v.p ? (void *)((uint4 *)v.p + r * stride) : nullptr;
+    o.norm = v.norm ? v.norm + r * nstride : nullptr;
+    return o;
+}
+
+template <class T>
+__device__ __forceinline__ void axpby_sp(Spinor<T> &o, T a, const Spinor<T> &x, T b, const Spinor<T> &y)
+{
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) o.s[s][i] = mk(a * x.s[s][i].r + b * y.s[s][i].r, a * x.s[s][i].i + b * y.s[s][i].i);
+}
+
+}  // namespace qcd

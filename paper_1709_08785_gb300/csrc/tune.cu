@@ -1,0 +1,229 @@
+// Autotuner for the stencil kernels: for each launch configuration the
+// solvers use (precision, mode, fused reduction, dagger, right-hand sides) it
+// times every candidate -- register budget (compiler's / capped at 80) x
+// threads per block along the sites -- on scratch buffers with L2 evicted
+// before each launch, keeps the fastest, and stores the choice in a JSON
+// cache keyed by device name, lattice and configuration.  Launches that have
+// no tuned entry use the default (compiler's budget, 128 sites per block).
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "blas.cuh"
+
+namespace qcd {
+
+namespace {
+
+std::string cache_prefix(qcd_ctx *c)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        std::strcpy(prop.name, "unknown");
+    }
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s|%dx%dx%dx%d|", prop.name, c->g.L[0], c->g.L[1], c->g.L[2], c->g.L[3]);
+    return buf;
+}
+
+// The cache is a JSON object with one entry per line:
+//   "<device>|<Lx>x<Ly>x<Lz>x<Lt>|<key>": [variant, bx, microseconds],
+using Cache = std::map<std::string, qcd_ctx::TuneEntry>;
+
+Cache read_cache(const char *path)
+{
+    Cache m;
+    if (!path) return m;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return m;
+    char line[1024], key[768];
+    while (std::fgets(line, sizeof(line), f)) {
+        qcd_ctx::TuneEntry e;
+        if (std::sscanf(line, " \"%767[^\"]\" : [ %d , %d , %lf ]", key, &e.variant, &e.bx, &e.us) == 4) m[key] = e;
+    }
+    std::fclose(f);
+    return m;
+}
+
+int write_cache(const char *path, const Cache &m)
+{
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) {
+        set_error_message("cannot write the tuning cache %s", path);
+        return QCD_EINVAL;
+    }
+    std::fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto &kv : m) {
+        std::fprintf(f, "  \"%s\": [%d, %d, %.3f]%s\n", kv.first.c_str(), kv.second.variant, kv.second.bx,
+                     kv.second.us, ++i < m.size() ? "," : "");
+    }
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    if (std::rename(tmp.c_str(), path) != 0) {
+        set_error_message("cannot replace the tuning cache %s", path);
+        return QCD_EINVAL;
+    }
+    return QCD_OK;
+}
+
+// scratch: nrhs input and nrhs output vectors of one precision
+int tune_buffers(qcd_ctx *c, int prec, int nrhs, HVec *in, HVec *out)
+{
+    const size_t hb = hvec_bytes(c->g, prec);
+    const size_t nb = (size_t)c->g.Vh_pad * sizeof(float);
+    const size_t need = 2 * nrhs * (hb + nb);
+    if (c->tune_bytes < need) {
+        if (c->tune_buf) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->tune_buf);
+            for (auto &p : c->pool)
+                if (p == c->tune_buf) p = nullptr;
+            c->tune_buf = nullptr;
+            c->tune_bytes = 0;
+        }
+        int rc = dev_alloc(c, &c->tune_buf, need);
+        if (rc) return rc;
+        c->tune_bytes = need;
+    }
+    char *base = (char *)c->tune_buf;
+    in->prec = out->prec = prec;
+    in->p = base;
+    out->p = base + nrhs * hb;
+    in->norm = (float *)(base + 2 * nrhs * hb);
+    out->norm = (float *)(base + 2 * nrhs * hb + nrhs * nb);
+    return fill_pattern(c, prec, *in, nrhs, hvec_elems(c->g, prec), 11);
+}
+
+int time_candidate(qcd_ctx *c, const StencilCall &s, double *us)
+{
+    const size_t flush_bytes = 256u << 20;
+    int rc;
+    if (!c->flush_buf && (rc = dev_alloc(c, &c->flush_buf, flush_bytes))) return rc;
+    cudaEvent_t e0, e1;
+    QCD_CUDA_CHECK(cudaEventCreate(&e0));
+    QCD_CUDA_CHECK(cudaEventCreate(&e1));
+    double best = 1e30;
+    for (int it = -1; it < 3; ++it) {
+        QCD_CUDA_CHECK(cudaMemsetAsync(c->flush_buf, it & 0xff, flush_bytes, c->stream));
+        QCD_CUDA_CHECK(cudaEventRecord(e0, c->stream));
+        if ((rc = launch_stencil(c, s))) break;
+        QCD_CUDA_CHECK(cudaEventRecord(e1, c->stream));
+        QCD_CUDA_CHECK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        QCD_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+        if (it >= 0 && ms * 1e3 < best) best = ms * 1e3;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    *us = best;
+    return QCD_OK;
+}
+
+int tune_one(qcd_ctx *c, StencilCall s, qcd_ctx::TuneEntry *out)
+{
+    HVec in, o;
+    int rc = tune_buffers(c, s.prec, s.nrhs, &in, &o);
+    if (rc) return rc;
+    s.in = in;
+    s.out = o;
+    s.y = in;
+    s.aux = in;
+    s.z = in;
+    s.rhs_stride = hvec_elems(c->g, s.prec);
+    s.norm_stride = (size_t)c->g.Vh_pad;
+    s.red_args = RedArgs{c->partials, c->counters, c->states + ST_TUNE, FIN_NONE};
+    s.done = nullptr;
+    const int nv = s.prec == QCD_F64 ? 1 : 2;
+    const int bxs1[] = {64, 128, 256}, bxsn[] = {32, 64};
+    const int *bxs = s.nrhs > 1 ? bxsn : bxs1;
+    const int nbx = s.nrhs > 1 ? 2 : 3;
+    qcd_ctx::TuneEntry best{0, 128, 1e30};
+    for (int v = 0; v < nv; ++v)
+        for (int k = 0; k < nbx; ++k) {
+            const int bx = bxs[k];
+            if (bx * s.nrhs > 384) continue;
+            if (s.red != R_NONE && (int)nblocks(c->g.Vh, bx) > c->partial_blocks) continue;
+            s.force_variant = v;
+            s.force_bx = bx;
+            double us;
+            if ((rc = time_candidate(c, s, &us))) return rc;
+            if (us < best.us) best = qcd_ctx::TuneEntry{v, bx, us};
+        }
+    *out = best;
+    return QCD_OK;
+}
+
+}  // namespace
+
+int autotune(qcd_ctx *c, const char *cache_path)
+{
+    if (!c->have_clover) {
+        set_error_message("qcd_autotune needs the gauge field and the clover term");
+        return QCD_ESTATE;
+    }
+    struct Cfg {
+        int prec, mode, red, nrhs;
+    };
+    const Cfg cfgs[] = {
+        {QCD_F64, M_MULT, R_NONE, 1},  {QCD_F64, M_DHAT, R_DOT_AUX, 1}, {QCD_F64, M_DHAT, R_OMEGA, 1},
+        {QCD_F64, M_SRC, R_NONE, 1},   {QCD_F64, M_FULL, R_NORM, 1},    {QCD_F64, M_DHAT, R_NORM, 1},
+        {QCD_F32, M_MULT, R_NONE, 1},  {QCD_F32, M_DHAT, R_DOT_AUX, 1}, {QCD_F32, M_DHAT, R_OMEGA, 1},
+        {QCD_F32, M_HOP, R_NONE, 1},   {QCD_F32, M_MULT, R_NONE, 12},
+        {QCD_F16, M_MULT, R_NONE, 1},  {QCD_F16, M_DHAT, R_DOT_AUX, 1}, {QCD_F16, M_DHAT, R_OMEGA, 1},
+        {QCD_F16, M_MULT, R_NONE, 12},
+    };
+    Cache cache = read_cache(cache_path);
+    const std::string prefix = cache_prefix(c);
+    bool changed = false;
+    const bool prof = c->profiling;
+    c->profiling = false;
+    int rc = QCD_OK;
+    for (const Cfg &f : cfgs) {
+        StencilCall s;
+        s.prec = f.prec;
+        s.mode = f.mode;
+        s.red = f.red;
+        s.nrhs = f.nrhs;
+        s.out_par = 0;
+        s.a = 1.0;
+        s.cc = -c->kappa * c->kappa;
+        const unsigned key = tune_key(s);
+        const std::string ck = prefix + std::to_string(key);
+        auto hit = cache.find(ck);
+        if (hit != cache.end()) {
+            c->tune[key] = hit->second;
+            continue;
+        }
+        qcd_ctx::TuneEntry e;
+        if ((rc = tune_one(c, s, &e))) break;
+        c->tune[key] = e;
+        cache[ck] = e;
+        changed = true;
+    }
+    c->profiling = prof;
+    if (rc) return rc;
+    if (cache_path && changed) return write_cache(cache_path, cache);
+    return QCD_OK;
+}
+
+int tune_entries(qcd_ctx *c, int max, unsigned *keys, int *variant, int *bx, double *us)
+{
+    int n = 0;
+    for (const auto &kv : c->tune) {
+        if (n < max) {
+            if (keys) keys[n] = kv.first;
+            if (variant) variant[n] = kv.second.variant;
+            if (bx) bx[n] = kv.second.bx;
+            if (us) us[n] = kv.second.us;
+        }
+        ++n;
+    }
+    return n;
+}
+
+}  // namespace qcd

@@ -66,7 +66,7 @@ EXPORTS = [
     "qcd_clover_apply", "qcd_mult_eo", "qcd_dhat", "qcd_dirac", "qcd_solve_opts_default", "qcd_solve",
     "qcd_set_profiling", "qcd_kernel_stats", "qcd_reset_kernel_stats", "qcd_strerror", "qcd_last_error",
     "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_dslash_eo_noalloc", "qcd_solve_adjoint",
-    "qcd_force",
+    "qcd_force", "qcd_autotune", "qcd_tune_info", "qcd_solve_batched", "qcd_set_wait_limit", "qcd_set_graphs",
 ]
 
 _lib = None
@@ -118,6 +118,13 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.qcd_mult_benchmark.argtypes = [vp, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
     lib.qcd_solve_adjoint.argtypes = [vp, vp, vp, dp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
     lib.qcd_force.argtypes = [vp, vp, vp, vp, vp]
+    lib.qcd_solve_batched.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                      ctypes.POINTER(dp), ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
+    lib.qcd_set_wait_limit.argtypes = [ctypes.c_longlong]
+    lib.qcd_set_graphs.argtypes = [ip]
+    lib.qcd_autotune.argtypes = [vp, ctypes.c_char_p]
+    lib.qcd_tune_info.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                  ctypes.POINTER(dp)]
     _lib = lib
     return lib
 
@@ -159,6 +166,35 @@ def default_opts(**kw) -> SolveOpts:
         else:
             setattr(o, k, int(v) if isinstance(getattr(o, k), int) else v)
     return o
+
+
+def solve_batched(ctxs, bs, xs, tols, opts: SolveOpts | None = None, check: bool = True, **kw) -> list:
+    """Solve problem i on ctxs[i] (b = bs[i], x = xs[i], device tensors) for all
+    i in one batched persistent-kernel run; returns one info dict per problem."""
+    lib = load_library()
+    n = len(ctxs)
+    if opts is None:
+        opts = default_opts(**kw)
+    H = (ctypes.c_void_p * n)(*[c._h.value for c in ctxs])
+    B = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    T = (ctypes.c_double * n)(*[float(t) for t in tols])
+    infos = (SolveInfo * n)()
+    rc = lib.qcd_solve_batched(H, n, B, X, T, ctypes.byref(opts), infos)
+    if check:
+        _check(rc)
+    out = [infos[i].as_dict() for i in range(n)]
+    for d in out:
+        d["rc"] = rc
+    return out
+
+
+def set_wait_limit(spins: int):
+    _check(load_library().qcd_set_wait_limit(int(spins)))
+
+
+def set_graphs(on: bool):
+    _check(load_library().qcd_set_graphs(int(on)))
 
 
 class Context:
@@ -262,6 +298,23 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.qcd_launch_count(self._h))
+
+    def autotune(self, cache_path: str | None = None):
+        """Tune the operator kernels' launch configurations (cached in JSON)."""
+        _check(self.lib.qcd_autotune(self._h, cache_path.encode() if cache_path else None))
+
+    def tune_info(self) -> list:
+        n = self.lib.qcd_tune_info(self._h, 0, None, None, None, None)
+        keys = (ctypes.c_uint * max(n, 1))()
+        var, thr = (ctypes.c_int * max(n, 1))(), (ctypes.c_int * max(n, 1))()
+        us = (ctypes.c_double * max(n, 1))()
+        self.lib.qcd_tune_info(self._h, n, keys, var, thr, us)
+        out = []
+        for i in range(n):
+            k = keys[i]
+            out.append(dict(key=k, prec=k & 3, mode=(k >> 2) & 7, red=(k >> 5) & 3, dagger=(k >> 7) & 1,
+                            nrhs=k >> 8, variant=var[i], threads=thr[i], us=us[i]))
+        return out
 
     def mult_benchmark(self, prec: int = F32, nrhs: int = 1, iters: int = 20) -> dict:
         ms, by = ctypes.c_double(0), ctypes.c_double(0)
