@@ -374,7 +374,8 @@ def run_dslash_only(args):
     ctx.autotune(TUNE_CACHE)
     hbm, kind = peaks()
     out = {"mode": "dslash-only", "lattice": list(dims), "peak_gbs": hbm, "peak_kind": kind}
-    for name, p, nrhs in (("f32", qcd.F32, 1), ("f16", qcd.F16, 1), ("f64", qcd.F64, 1), ("f32_12rhs", qcd.F32, 12)):
+    for name, p, nrhs in (("f32", qcd.F32, 1), ("f16", qcd.F16, 1), ("f64", qcd.F64, 1), ("df64", qcd.DF64, 1),
+                          ("f32_12rhs", qcd.F32, 12)):
         r = ctx.mult_benchmark(p, nrhs, max(3, args.steps))
         out[name] = {"gbs": round(r["gbs"], 1), "frac_hbm": round(r["gbs"] / hbm, 3), "us": round(r["ms"] * 1e3, 2),
                      "bytes": r["bytes"]}

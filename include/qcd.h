@@ -70,7 +70,11 @@ typedef enum {
     QCD_ESTATE = -9             /* call out of order (e.g. no gauge field loaded) */
 } qcd_status;
 
-typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2 } qcd_prec;
+/* QCD_DF64: FP64-sized storage, arithmetic in pairs of floats (double-float,
+ * about 48 significant bits): the outer level of the mixed solvers, since
+ * GB300 issues FP32 at about 64x its FP64 rate.  Operator calls with
+ * QCD_DF64 take complex128 buffers. */
+typedef enum { QCD_F64 = 0, QCD_F32 = 1, QCD_F16 = 2, QCD_DF64 = 3 } qcd_prec;
 
 /* Create a context for one lattice on the current CUDA device.
  * dims: host array of 4 even extents >= 2 (Lx*Ly*Lz*Lt < 2^31).
@@ -160,6 +164,9 @@ typedef struct {
     int max_inner[2];     /* iteration caps of the lower levels */
     int max_restarts;     /* restarts from the true residual (FP64) */
     int use_x0;           /* 1: x holds an initial guess; 0: x = 0 (Alg. 1) */
+    int outer_df64;       /* precision_levels >= 2: 1 (default) computes the
+                             outer level in QCD_DF64, 0 in FP64; the final
+                             true residual is FP64 either way */
 } qcd_solve_opts;
 
 typedef struct {
@@ -173,7 +180,8 @@ typedef struct {
 } qcd_solve_info;
 
 /* Defaults: precision_levels 2, even_odd 1, inner_tol {1e-5, 1e-2},
- * max_outer 200, max_inner {250, 250}, max_restarts 5, use_x0 0. */
+ * max_outer 200, max_inner {250, 250}, max_restarts 5, use_x0 0,
+ * outer_df64 1. */
 void qcd_solve_opts_default(qcd_solve_opts *opts);
 
 /* Solve D x = b to ||b - D x|| / ||b|| <= tol (recomputed in FP64 at exit;

@@ -203,8 +203,9 @@ extern "C" int qcd_create(qcd_ctx **out, const int dims[4], int t_bc, void *stre
         if ((rc = dev_alloc(c, &c->U32[p], vp * 12 * 16))) return fail(rc);
         if ((rc = dev_alloc(c, &c->U16a[p], vp * 4 * 16))) return fail(rc);
         if ((rc = dev_alloc(c, &c->U16b[p], vp * 4 * 8))) return fail(rc);
-        const size_t cl[3] = {vp * 36 * 16, vp * 18 * 16, vp * 9 * 16};
-        for (int q = 0; q < 3; ++q) {
+        if ((rc = dev_alloc(c, &c->UDF[p], vp * 36 * 16))) return fail(rc);
+        const size_t cl[4] = {vp * 36 * 16, vp * 18 * 16, vp * 9 * 16, vp * 36 * 16};
+        for (int q = 0; q < 4; ++q) {
             if ((rc = dev_alloc(c, &c->C[q][p], cl[q]))) return fail(rc);
             if ((rc = dev_alloc(c, &c->Ci[q][p], cl[q]))) return fail(rc);
         }
@@ -341,7 +342,7 @@ int check_op_args(qcd_ctx *c, void *out, const void *in, int prec, int nrhs, boo
         set_error_message("null argument");
         return QCD_EINVAL;
     }
-    if (prec < QCD_F64 || prec > QCD_F16 || nrhs < 1) {
+    if (prec < QCD_F64 || prec > QCD_DF64 || nrhs < 1) {
         set_error_message("bad precision %d or nrhs %d", prec, nrhs);
         return QCD_EINVAL;
     }
@@ -361,7 +362,7 @@ constexpr int RHS_TILE = 16;
 // shared body of dslash / mult / dhat / clover on canonical half vectors
 int op_half(qcd_ctx *c, void *out, const void *in, int prec, int nrhs, int kind, int out_par, int dagger, int inverse)
 {
-    const bool f32io = prec != QCD_F64;
+    const bool f32io = prec == QCD_F32 || prec == QCD_F16;
     const size_t cbytes = (size_t)c->g.Vh * 12 * (f32io ? 8 : 16);
     for (int r0 = 0; r0 < nrhs; r0 += RHS_TILE) {
         const int nr = nrhs - r0 < RHS_TILE ? nrhs - r0 : RHS_TILE;
@@ -484,6 +485,7 @@ extern "C" void qcd_solve_opts_default(qcd_solve_opts *o)
     o->max_inner[1] = 250;
     o->max_restarts = 5;
     o->use_x0 = 0;
+    o->outer_df64 = 1;
 }
 
 extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const qcd_solve_opts *opts,
@@ -684,7 +686,7 @@ extern "C" int qcd_tune_info(qcd_ctx *c, int max, unsigned *keys, int *variant, 
 extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, double *ms_per_launch,
                                   double *bytes_per_launch)
 {
-    if (!c || !ms_per_launch || !bytes_per_launch || prec < QCD_F64 || prec > QCD_F16 || nrhs < 1 || nrhs > 16 ||
+    if (!c || !ms_per_launch || !bytes_per_launch || prec < QCD_F64 || prec > QCD_DF64 || nrhs < 1 || nrhs > 16 ||
         iters < 1) {
         set_error_message("invalid benchmark arguments");
         return QCD_EINVAL;

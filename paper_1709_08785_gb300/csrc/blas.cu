@@ -47,7 +47,7 @@ static int run(qcd_ctx *c, int nsites, const Op &op, int fin, SolverState *st, c
     return QCD_OK;
 }
 
-static double sp_bytes(int prec) { return prec == QCD_F64 ? 192.0 : prec == QCD_F32 ? 96.0 : 52.0; }
+static double sp_bytes(int prec) { return prec == QCD_F32 ? 96.0 : prec == QCD_F16 ? 52.0 : 192.0; }
 
 // ---------------------------------------------------------------- state
 __global__ void k_state_init(SolverState *st, double tol2, double tol2_rel, int maxit, double bd_eps, int unit)
@@ -78,6 +78,7 @@ __global__ void k_set_tol2(SolverState *dst, const SolverState *src, int slot, d
     switch (p) {                                             \
     case QCD_F64: { constexpr int P = QCD_F64; __VA_ARGS__; } \
     case QCD_F32: { constexpr int P = QCD_F32; __VA_ARGS__; } \
+    case QCD_DF64: { constexpr int P = QCD_DF64; __VA_ARGS__; } \
     default: { constexpr int P = QCD_F16; __VA_ARGS__; }      \
     }
 
@@ -177,6 +178,9 @@ int blas_inner_init(qcd_ctx *c, int ps, int pd, int n, HVec src, const double *s
     if (ps == QCD_F64 && pd == QCD_F16)
         return run<0>(c, n, OpInner<QCD_F64, QCD_F16>{src.sp(), r.sp(), rt.sp(), p.sp(), x.sp(), src_norm2}, FIN_NONE,
                       nullptr, done, QCD_K_BLAS, by);
+    if (ps == QCD_DF64 && pd == QCD_F32)
+        return run<0>(c, n, OpInner<QCD_DF64, QCD_F32>{src.sp(), r.sp(), rt.sp(), p.sp(), x.sp(), src_norm2}, FIN_NONE,
+                      nullptr, done, QCD_K_BLAS, by);
     set_error_message("unsupported precision pair %d -> %d", ps, pd);
     return QCD_EINVAL;
 }
@@ -190,6 +194,9 @@ int blas_lift(qcd_ctx *c, int ps, int pd, int n, HVec x, HVec v, const double *s
         return run<0>(c, n, OpLift<QCD_F16, QCD_F32>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, QCD_K_BLAS, by);
     if (ps == QCD_F16 && pd == QCD_F64)
         return run<0>(c, n, OpLift<QCD_F16, QCD_F64>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, QCD_K_BLAS, by);
+    if (ps == QCD_F32 && pd == QCD_DF64)
+        return run<0>(c, n, OpLift<QCD_F32, QCD_DF64>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, QCD_K_BLAS,
+                      by);
     set_error_message("unsupported precision pair %d -> %d", ps, pd);
     return QCD_EINVAL;
 }
@@ -255,7 +262,7 @@ __global__ void k_half_to_canon(Geom g, SpinorPtr src, TC *__restrict__ dst, int
 
 size_t hvec_elems(const Geom &g, int prec)  // 16-byte elements of one half vector
 {
-    const int nc = prec == QCD_F64 ? 12 : prec == QCD_F32 ? 6 : 3;
+    const int nc = prec == QCD_F32 ? 6 : prec == QCD_F16 ? 3 : 12;
     return (size_t)g.Vh_pad * nc;
 }
 
@@ -329,6 +336,32 @@ int fill_pattern(qcd_ctx *c, int prec, HVec v, int nrhs, size_t rhs_stride, int 
     return QCD_OK;
 }
 
+// one half vector from one precision to another
+template <int PS, int PD>
+struct OpConvert {
+    SpinorPtr src, dst;
+    __device__ void operator()(int cb, double *) const
+    {
+        Spinor<typename Prec<PS>::T> S;
+        Prec<PS>::load(src, cb, S);
+        Spinor<typename Prec<PD>::T> D;
+        cvt_sp(D, S);
+        Prec<PD>::store(dst, cb, D);
+    }
+};
+
+int convert_half(qcd_ctx *c, HVec src, HVec dst)
+{
+    const int n = c->g.Vh_pad;
+    const double by = (sp_bytes(src.prec) + sp_bytes(dst.prec)) * n;
+    if (src.prec == QCD_F64 && dst.prec == QCD_DF64)
+        return run<0>(c, n, OpConvert<QCD_F64, QCD_DF64>{src.sp(), dst.sp()}, FIN_NONE, nullptr, nullptr, QCD_K_BLAS, by);
+    if (src.prec == QCD_DF64 && dst.prec == QCD_F64)
+        return run<0>(c, n, OpConvert<QCD_DF64, QCD_F64>{src.sp(), dst.sp()}, FIN_NONE, nullptr, nullptr, QCD_K_BLAS, by);
+    set_error_message("unsupported conversion %d -> %d", src.prec, dst.prec);
+    return QCD_EINVAL;
+}
+
 // ---------------------------------------------------------------- clover apply
 template <int P>
 __global__ void k_clover_apply(Geom g, CloverPtr C, int par, SpinorPtr in, SpinorPtr out, size_t rhs_stride,
@@ -354,7 +387,7 @@ int clover_apply_half(qcd_ctx *c, int prec, int parity, int inverse, HVec in, HV
     CloverPtr C;
     for (int p = 0; p < 2; ++p) C.p[p] = inverse ? c->Ci[prec][p] : c->C[prec][p];
     dim3 grid(nblocks(c->g.Vh, 128), nrhs);
-    const double cl = prec == QCD_F64 ? 576 : prec == QCD_F32 ? 288 : 144;
+    const double cl = prec == QCD_F32 ? 288 : prec == QCD_F16 ? 144 : 576;
     ProfScope prof(c, QCD_K_OTHER, (cl + 2 * nrhs * sp_bytes(prec)) * c->g.Vh);
     PREC_SWITCH(prec, k_clover_apply<P><<<grid, 128, 0, c->stream>>>(c->g, C, parity, in.sp(), out.sp(), rhs_stride,
                                                                     (size_t)c->g.Vh_pad);

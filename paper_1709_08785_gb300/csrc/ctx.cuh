@@ -76,11 +76,12 @@ struct qcd_ctx {
     void *U32[2] = {nullptr, nullptr};
     void *U16a[2] = {nullptr, nullptr};
     void *U16b[2] = {nullptr, nullptr};
+    void *UDF[2] = {nullptr, nullptr};  // DF64: 18 reals as float pairs
     bool have_gauge = false;
 
     // clover term F and inverse, [precision][parity]
-    void *C[3][2] = {};
-    void *Ci[3][2] = {};
+    void *C[4][2] = {};
+    void *Ci[4][2] = {};
     bool have_clover = false;
     double kappa = 0.0, csw = 0.0;
 
@@ -94,7 +95,7 @@ struct qcd_ctx {
 
     // workspace vectors, allocated on first use
     std::vector<void *> pool;
-    qcd::HVec work[3][16];  // [precision][slot]
+    qcd::HVec work[4][16];  // [precision][slot]
     void *staging = nullptr;        // canonical full-lattice complex128 staging
     size_t staging_bytes = 0;
 
@@ -189,6 +190,7 @@ int fill_pattern(qcd_ctx *c, int prec, HVec v, int nrhs, size_t rhs_stride, int 
 
 // blas.cu -- conversions between canonical and internal layouts
 int canon_to_half(qcd_ctx *c, int prec, int src_is_f32, const void *src, int parity_full, HVec dst, int nrhs, size_t rhs_stride);
+int convert_half(qcd_ctx *c, HVec src, HVec dst);  // between precisions, one half vector
 int half_to_canon(qcd_ctx *c, int prec, int dst_is_f32, HVec src, void *dst, int parity_full, int nrhs, size_t rhs_stride);
 int clover_apply_half(qcd_ctx *c, int prec, int parity, int inverse, HVec in, HVec out, int nrhs, size_t rhs_stride);
 

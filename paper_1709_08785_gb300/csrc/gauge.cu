@@ -16,8 +16,15 @@
 namespace qcd {
 
 // ---------------------------------------------------------------- links
+__device__ __forceinline__ float4 df_pair(double2 z)
+{
+    const df r(z.x), i(z.y);
+    return make_float4(r.hi, r.lo, i.hi, i.lo);
+}
+
 __global__ void k_gauge_convert(Geom g, const double2 *__restrict__ U, double2 *U64e, double2 *U64o, float4 *U32e,
-                                float4 *U32o, uint4 *U16ae, uint4 *U16ao, uint2 *U16be, uint2 *U16bo)
+                                float4 *U32o, uint4 *U16ae, uint4 *U16ao, uint2 *U16be, uint2 *U16bo, float4 *UDFe,
+                                float4 *UDFo)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
@@ -36,6 +43,8 @@ __global__ void k_gauge_convert(Geom g, const double2 *__restrict__ U, double2 *
         double2 m[9];
         for (int k = 0; k < 9; ++k) m[k] = U[((size_t)s * 4 + mu) * 9 + k];
         for (int k = 0; k < 9; ++k) u64[soa(cb, 36, mu * 9 + k)] = m[k];
+        float4 *udf = par ? UDFo : UDFe;
+        for (int k = 0; k < 9; ++k) udf[soa(cb, 36, mu * 9 + k)] = df_pair(m[k]);
         // first two columns: a = (m00, m10, m20), b = (m01, m11, m21)
         const double2 a0 = m[0], a1 = m[3], a2 = m[6], b0 = m[1], b1 = m[4], b2 = m[7];
         u32[soa(cb, 12, mu * 3 + 0)] = make_float4(a0.x, a0.y, a1.x, a1.y);
@@ -51,7 +60,8 @@ int gauge_convert(qcd_ctx *c, const void *U_dev)
 {
     k_gauge_convert<<<nblocks(c->g.V, 256), 256, 0, c->stream>>>(
         c->g, (const double2 *)U_dev, (double2 *)c->U64[0], (double2 *)c->U64[1], (float4 *)c->U32[0],
-        (float4 *)c->U32[1], (uint4 *)c->U16a[0], (uint4 *)c->U16a[1], (uint2 *)c->U16b[0], (uint2 *)c->U16b[1]);
+        (float4 *)c->U32[1], (uint4 *)c->U16a[0], (uint4 *)c->U16a[1], (uint2 *)c->U16b[0], (uint2 *)c->U16b[1],
+        (float4 *)c->UDF[0], (float4 *)c->UDF[1]);
     QCD_CUDA_CHECK(cudaGetLastError());
     return QCD_OK;
 }
@@ -223,7 +233,8 @@ __device__ bool herm_inverse6(const cx<double> A[6][6], cx<double> Ai[6][6])
 }
 
 // store one block (diag reals then the lower triangle) in all precisions
-__device__ void store_block(const cx<double> A[6][6], int blk, int cb, double2 *p64, float4 *p32, uint4 *p16)
+__device__ void store_block(const cx<double> A[6][6], int blk, int cb, double2 *p64, float4 *p32, uint4 *p16,
+                            float4 *pdf)
 {
     double r[36];
     for (int i = 0; i < 6; ++i) r[i] = A[i][i].r;
@@ -235,6 +246,7 @@ __device__ void store_block(const cx<double> A[6][6], int blk, int cb, double2 *
             ++k;
         }
     for (int q = 0; q < 18; ++q) p64[soa(cb, 36, blk * 18 + q)] = make_double2(r[2 * q], r[2 * q + 1]);
+    for (int q = 0; q < 18; ++q) pdf[soa(cb, 36, blk * 18 + q)] = df_pair(make_double2(r[2 * q], r[2 * q + 1]));
     for (int q = 0; q < 9; ++q)
         p32[soa(cb, 18, blk * 9 + q)] = make_float4((float)r[4 * q], (float)r[4 * q + 1], (float)r[4 * q + 2], (float)r[4 * q + 3]);
     // halves: element e of the site = blk*36 + j; uint4 q holds elements 8q..8q+7
@@ -247,7 +259,7 @@ __device__ void store_block(const cx<double> A[6][6], int blk, int cb, double2 *
 }
 
 __global__ void k_clover_build(Geom g, GaugePtr U, int par, double ck, double2 *F64, float4 *F32, uint4 *F16,
-                               double2 *Fi64, float4 *Fi32, uint4 *Fi16, int *bad)
+                               float4 *FDF, double2 *Fi64, float4 *Fi32, uint4 *Fi16, float4 *FiDF, int *bad)
 {
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= g.Vh) return;
@@ -274,14 +286,14 @@ __global__ void k_clover_build(Geom g, GaugePtr U, int par, double ck, double2 *
                 A[j][i] = conj(m);
             }
         }
-        store_block(A, blk, cb, F64, F32, F16);
+        store_block(A, blk, cb, F64, F32, F16, FDF);
         cx<double> Ai[6][6];
         if (!herm_inverse6(A, Ai)) {
             atomicExch(bad, 1);
             for (int i = 0; i < 6; ++i)
                 for (int j = 0; j < 6; ++j) Ai[i][j] = mk(0.0, 0.0);
         }
-        store_block(Ai, blk, cb, Fi64, Fi32, Fi16);
+        store_block(Ai, blk, cb, Fi64, Fi32, Fi16, FiDF);
     }
 }
 
@@ -296,8 +308,9 @@ int clover_build(qcd_ctx *c, double kappa, double csw)
     for (int par = 0; par < 2; ++par) {
         k_clover_build<<<nblocks(c->g.Vh, 64), 64, 0, c->stream>>>(
             c->g, U, par, csw * kappa, (double2 *)c->C[QCD_F64][par], (float4 *)c->C[QCD_F32][par],
-            (uint4 *)c->C[QCD_F16][par], (double2 *)c->Ci[QCD_F64][par], (float4 *)c->Ci[QCD_F32][par],
-            (uint4 *)c->Ci[QCD_F16][par], c->flag_dev);
+            (uint4 *)c->C[QCD_F16][par], (float4 *)c->C[QCD_DF64][par], (double2 *)c->Ci[QCD_F64][par],
+            (float4 *)c->Ci[QCD_F32][par], (uint4 *)c->Ci[QCD_F16][par], (float4 *)c->Ci[QCD_DF64][par],
+            c->flag_dev);
         QCD_CUDA_CHECK(cudaGetLastError());
     }
     int bad = 0;

@@ -120,6 +120,69 @@ __device__ __forceinline__ void fmac_(cx<T> &a, cx<T> b, cx<T> c)
     a.i = fma(-b.i, c.r, a.i);
 }
 
+// ---------------------------------------------------------------- double-float
+// A real as an unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
+// about 48 significant bits, with the error-free transformations of Dekker
+// and Knuth (TwoSum, FastTwoSum, TwoProd through FMA).  The outer level of
+// the mixed solvers computes in it: GB300 issues FP32 at ~64x its FP64 rate,
+// so ~15 FP32 instructions per multiply-add still beat one FP64 one.
+struct df {
+    float hi, lo;
+    df() = default;
+    __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ df(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ df(float f) : hi(f), lo(0.f) {}
+    __host__ __device__ df(int i) : hi((float)i), lo(0.f) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ df fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return df(s, b - (s - a));
+}
+
+__device__ __forceinline__ df operator+(df a, df b)
+{
+    // TwoSum of the high parts, then the low parts folded in (the "sloppy"
+    // sum: its error is relative to |a| + |b|, which is what the operator
+    // and the BLAS updates need)
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    return fast_two_sum(s, e);
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df &operator+=(df &a, df b) { return a = a + b; }
+__device__ __forceinline__ df fma(df a, df b, df c)
+{
+    // a*b + c: TwoProd, then TwoSum with c
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = p + c.hi;
+    const float bb = s - p;
+    float f = (p - (s - bb)) + (c.hi - bb);
+    f += e + c.lo;
+    return fast_two_sum(s, f);
+}
+
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(df x) { return (double)x; }
+
 template <class T>
 struct Spinor {
     cx<T> s[4][3];
@@ -348,6 +411,50 @@ struct Prec<QCD_F16> {
         for (int k = 0; k < 6; ++k) d[k] = r[k];
 #pragma unroll
         for (int k = 0; k < 15; ++k) o[k] = mk(r[6 + 2 * k], r[7 + 2 * k]);
+    }
+};
+
+// DF64: FP64-sized storage, each real as the float pair (hi, lo) of the
+// double-float type; a float4 holds one complex number (spinors, links) or
+// two reals (clover), in the same site-blocked order as the FP64 layout.
+__device__ __forceinline__ cx<df> f4c(float4 f) { return mk(df(f.x, f.y), df(f.z, f.w)); }
+__device__ __forceinline__ float4 c4f(cx<df> c) { return make_float4(c.r.hi, c.r.lo, c.i.hi, c.i.lo); }
+
+template <>
+struct Prec<QCD_DF64> {
+    using T = df;
+    static constexpr int SP_NC = 12, LK_NC = 9, CL_NC = 36;
+
+    static __device__ __forceinline__ void load(const SpinorPtr &v, int cb, Spinor<T> &s)
+    {
+        const float4 *p = (const float4 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s.s[k / 3][k % 3] = f4c(__ldg(p + soa(cb, 12, k)));
+    }
+    static __device__ __forceinline__ void store(const SpinorPtr &v, int cb, const Spinor<T> &s)
+    {
+        float4 *p = (float4 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[soa(cb, 12, k)] = c4f(s.s[k / 3][k % 3]);
+    }
+    static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
+    {
+        const float4 *p = (const float4 *)g.a[par];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) U.u[k / 3][k % 3] = f4c(__ldg(p + soa(cb, 36, mu * 9 + k)));
+    }
+    static __device__ __forceinline__ void load_clover(const CloverPtr &c, int par, int cb, int blk, T d[6], cx<T> o[15])
+    {
+        const float4 *p = (const float4 *)c.p[par];
+        const int k0 = blk * 18;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 v = __ldg(p + soa(cb, 36, k0 + k));
+            d[2 * k] = df(v.x, v.y);
+            d[2 * k + 1] = df(v.z, v.w);
+        }
+#pragma unroll
+        for (int k = 0; k < 15; ++k) o[k] = f4c(__ldg(p + soa(cb, 36, k0 + 3 + k)));
     }
 };
 

@@ -173,14 +173,14 @@ int flexible(Solver &S, int lev)
         TRY(precondition(S, lev + 1, L.p, L.prec, &L.st->norm2[1], L.v, done));      // v = M p
         TRY(dhat(c, L.prec, L.v, L.q, L.tmp, R_DOT_AUX, L.rt, L.st, FIN_ALPHA, done));  // q = D^ v, alpha
         TRY(blas_flex1(c, L.prec, n, L.x, L.v, L.r, L.q, L.st));                       // x, r, |r|
-        S.info.dhat_applies[L.prec] += 1;
+        S.info.dhat_applies[L.prec == QCD_DF64 ? QCD_F64 : L.prec] += 1;  // DF64 counts as the FP64 level
         TRY(read_state(c, L.slot, &h));
         if (h.done) break;
         TRY(precondition(S, lev + 1, L.r, L.prec, &L.st->rr, L.v, done));                // v = M r
         TRY(dhat(c, L.prec, L.v, L.t, L.tmp, R_OMEGA, L.r, L.st, FIN_OMEGA, done));      // t = D^ v, omega
         TRY(blas_flex2(c, L.prec, n, L.x, L.v, L.r, L.t, L.rt, L.st));                  // x, r, beta
         TRY(blas_update_p(c, L.prec, n, L.p, L.r, L.q, L.st, FIN_SETN + 1));             // p, |p|
-        S.info.dhat_applies[L.prec] += 1;
+        S.info.dhat_applies[L.prec == QCD_DF64 ? QCD_F64 : L.prec] += 1;
         TRY(read_state(c, L.slot, &h));
         if (h.done) break;
     }
@@ -213,18 +213,19 @@ int precondition(Solver &S, int level, HVec src, int src_prec, const double *src
 
 int residual_eo(Solver &S, HVec xe, HVec out, SolverState *st, int fin)
 {
-    // out = b^ - D^ x_e = b^ - x_e + kappa^2 H~_eo H~_oe x_e
+    // out = b^ - D^ x_e = b^ - x_e + kappa^2 H~_eo H~_oe x_e, in the outer
+    // level's arithmetic
     qcd_ctx *c = S.c;
     Level &L = S.lv[0];
     StencilCall s1;
-    s1.prec = QCD_F64;
+    s1.prec = L.prec;
     s1.mode = M_MULT;
     s1.out_par = 1;
     s1.out = L.tmp;
     s1.in = xe;
     TRY(launch_stencil(c, s1));
     StencilCall s2;
-    s2.prec = QCD_F64;
+    s2.prec = L.prec;
     s2.mode = M_DHAT;
     s2.out_par = 0;
     s2.out = out;
@@ -267,13 +268,25 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     qcd_ctx *c = S.c;
     const int n = c->g.Vh_pad;
     Level &O = S.lv[0];
+    // The outer level computes in P0: FP64 for the plain BiCGStab, and for
+    // the nested schemes by default DF64 (float pairs, ~48 bits; GB300's
+    // FP64 rate is ~1/64 of its FP32 rate).  The final true-residual check
+    // is always FP64.
+    const int P0 = (S.o.precision_levels >= 2 && S.o.outer_df64) ? QCD_DF64 : QCD_F64;
     TRY(get_work(c, QCD_F64, 0, &S.be));
     TRY(get_work(c, QCD_F64, 1, &S.bo));
-    TRY(get_work(c, QCD_F64, 2, &S.bhat));
     TRY(get_work(c, QCD_F64, 3, &S.xo));
     TRY(get_work(c, QCD_F64, 4, &S.re));
     TRY(get_work(c, QCD_F64, 5, &S.ro));
-    TRY(get_level(c, O, QCD_F64, 6, ST_OUTER));
+    TRY(get_work(c, P0, 2, &S.bhat));
+    TRY(get_level(c, O, P0, 6, ST_OUTER));
+    HVec beP = S.be, boP = S.bo, xoP = S.xo, xe64 = O.x;
+    if (P0 != QCD_F64) {
+        TRY(get_work(c, P0, 0, &beP));
+        TRY(get_work(c, P0, 1, &boP));
+        TRY(get_work(c, P0, 3, &xoP));
+        TRY(get_work(c, QCD_F64, 6, &xe64));
+    }
     if (S.o.precision_levels >= 2) TRY(get_level(c, S.lv[1], QCD_F32, 0, ST_MID));
     if (S.o.precision_levels >= 3) TRY(get_level(c, S.lv[2], QCD_F16, 0, ST_INNER));
     S.aux = c->states + ST_AUX;
@@ -284,16 +297,20 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     TRY(state_init(c, S.aux, 0.0, 0.0, 0, 0.0, 0));
     TRY(blas_norm2(c, QCD_F64, n, S.be, S.aux, FIN_SETN + 0));
     TRY(blas_norm2(c, QCD_F64, n, S.bo, S.aux, FIN_ADDN + 0));
+    if (P0 != QCD_F64) {
+        TRY(convert_half(c, S.be, beP));
+        TRY(convert_half(c, S.bo, boP));
+    }
     // b^_e = F_ee^-1 (b_e + kappa H_eo F_oo^-1 b_o)   (Eq. 6, Alg. 1 line 3)
-    TRY(clover_apply_half(c, QCD_F64, 1, 1, S.bo, O.tmp, 1, 0));
+    TRY(clover_apply_half(c, P0, 1, 1, boP, O.tmp, 1, 0));
     {
         StencilCall s;
-        s.prec = QCD_F64;
+        s.prec = P0;
         s.mode = M_SRC;
         s.out_par = 0;
         s.out = S.bhat;
         s.in = O.tmp;
-        s.y = S.be;
+        s.y = beP;
         s.a = 1.0;
         s.cc = c->kappa;
         TRY(launch_stencil(c, s));
@@ -305,11 +322,11 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     TRY(state_init(c, O.st, 0.0, 0.0, maxit, BD_EPS_F64, 0));
     TRY(set_tol2(c, O.st, S.aux, 0, 0.25 * tol * tol));
     if (S.o.use_x0) {
-        TRY(canon_to_half(c, QCD_F64, 0, x, 0, O.x, 1, 0));
+        TRY(canon_to_half(c, P0, 0, x, 0, O.x, 1, 0));
         TRY(residual_eo(S, O.x, O.r, O.st, FIN_NONE));
-        TRY(blas_init(c, QCD_F64, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_INIT));
+        TRY(blas_init(c, P0, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_INIT));
     } else {
-        TRY(blas_init(c, QCD_F64, n, S.bhat, O.r, O.rt, O.p, O.x, 1, O.st, FIN_INIT));
+        TRY(blas_init(c, P0, n, S.bhat, O.r, O.rt, O.p, O.x, 1, O.st, FIN_INIT));
     }
     SolverState h, ha;
     int status = QCD_OK;
@@ -325,16 +342,20 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         status = h.status;
         // x_o = F_oo^-1 (b_o + kappa H_oe x_e)   (Eq. 7, Alg. 1 line 19)
         StencilCall s;
-        s.prec = QCD_F64;
+        s.prec = P0;
         s.mode = M_SRC;
         s.out_par = 1;
-        s.out = S.xo;
+        s.out = xoP;
         s.in = O.x;
-        s.y = S.bo;
+        s.y = boP;
         s.a = 1.0;
         s.cc = c->kappa;
         TRY(launch_stencil(c, s));
-        TRY(true_residual(S, O.x, S.xo));
+        if (P0 != QCD_F64) {
+            TRY(convert_half(c, O.x, xe64));
+            TRY(convert_half(c, xoP, S.xo));
+        }
+        TRY(true_residual(S, xe64, S.xo));
         TRY(read_state(c, ST_AUX, &ha));
         S.info.true_resid = resid_ratio(ha);
         if (!std::isfinite(S.info.true_resid)) {
@@ -355,11 +376,9 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         TRY(state_init(c, O.st, 0.0, 0.0, maxit, BD_EPS_F64, 0));
         TRY(set_tol2(c, O.st, S.aux, 0, 0.25 * tol * tol));
         TRY(residual_eo(S, O.x, O.r, O.st, FIN_NONE));
-        TRY(blas_init(c, QCD_F64, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_RESTART));
-        // keep the iteration count of the cap across restarts
-        TRY(read_state(c, O.slot, &h));
+        TRY(blas_init(c, P0, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_RESTART));
     }
-    TRY(half_to_canon(c, QCD_F64, 0, O.x, x, 0, 1, 0));
+    TRY(half_to_canon(c, QCD_F64, 0, xe64, x, 0, 1, 0));
     TRY(half_to_canon(c, QCD_F64, 0, S.xo, x, 1, 1, 0));
     return status;
 }

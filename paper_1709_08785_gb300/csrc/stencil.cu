@@ -34,11 +34,11 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
         const SpinorPtr in = rhs_ptr(A.in, r, A.rhs_stride, A.norm_stride);
         const SpinorPtr out = rhs_ptr(A.out, r, A.rhs_stride, A.norm_stride);
         Spinor<T> acc;
-        hopping<P, DAG>(A.g, A.U, in, A.out_par, cb, acc);
+        hopping_any<P, DAG>(A.g, A.U, in, A.out_par, cb, acc);
         if (MODE == M_MULT) {
-            apply_clover<P>(A.C, A.out_par, cb, acc);
+            clover_any<P>(A.C,A.out_par, cb, acc);
         } else if (MODE == M_DHAT) {
-            apply_clover<P>(A.C, A.out_par, cb, acc);
+            clover_any<P>(A.C,A.out_par, cb, acc);
             Spinor<T> y;
             Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
             axpby_sp(acc, T(A.cc), acc, T(A.a), y);
@@ -59,19 +59,19 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
                         di += o.r * v.i - o.i * v.r;
                         nn += o.r * o.r + o.i * o.i;
                     }
-                red[0] = dr;
-                red[1] = di;
-                red[2] = nn;
+                red[0] = to_d(dr);
+                red[1] = to_d(di);
+                red[2] = to_d(nn);
             }
         } else if (MODE == M_SRC) {
             Spinor<T> y;
             Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
             axpby_sp(acc, T(A.cc), acc, T(A.a), y);
-            apply_clover<P>(A.C, A.out_par, cb, acc);
+            clover_any<P>(A.C,A.out_par, cb, acc);
         } else if (MODE == M_FULL) {
             Spinor<T> y;
             Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
-            apply_clover<P>(A.C, A.out_par, cb, y);
+            clover_any<P>(A.C,A.out_par, cb, y);
             axpby_sp(acc, T(A.cc), acc, T(A.a), y);
             if (A.d != 0.0) {
                 Spinor<T> z;
@@ -91,15 +91,15 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
                     dr += a.r * o.r + a.i * o.i;
                     di += a.r * o.i - a.i * o.r;
                 }
-            red[0] = dr;
-            red[1] = di;
+            red[0] = to_d(dr);
+            red[1] = to_d(di);
         } else if (RED == R_NORM) {
             T nn = 0;
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
                 for (int i = 0; i < 3; ++i) nn += acc.s[s][i].r * acc.s[s][i].r + acc.s[s][i].i * acc.s[s][i].i;
-            red[0] = nn;
+            red[0] = to_d(nn);
         }
         Prec<P>::store(out, cb, acc);
     }
@@ -126,7 +126,7 @@ __global__ void __maxnreg__(80) stencil_kernel_r80(StencilArgs A)
 template <int P, int MODE, int RED, bool DAG>
 static void launch_t(const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int variant)
 {
-    if constexpr (P != QCD_F64) {
+    if constexpr (P == QCD_F32 || P == QCD_F16) {
         if (variant == 1) {
             stencil_kernel_r80<P, MODE, RED, DAG><<<grid, block, 0, s>>>(A);
             return;
@@ -173,7 +173,7 @@ static int dispatch(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3
 // once, the output written once), by precision: spinor, link, clover.
 static void site_bytes(int prec, double &spinor, double &link, double &clover)
 {
-    if (prec == QCD_F64) { spinor = 192; link = 144; clover = 576; }
+    if (prec == QCD_F64 || prec == QCD_DF64) { spinor = 192; link = 144; clover = 576; }
     else if (prec == QCD_F32) { spinor = 96; link = 48; clover = 288; }
     else { spinor = 52; link = 24; clover = 144; }
 }
@@ -204,7 +204,7 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
     A.g = c->g;
     const int p = sc.prec;
     for (int par = 0; par < 2; ++par) {
-        A.U.a[par] = p == QCD_F64 ? c->U64[par] : p == QCD_F32 ? c->U32[par] : c->U16a[par];
+        A.U.a[par] = p == QCD_F64 ? c->U64[par] : p == QCD_F32 ? c->U32[par] : p == QCD_DF64 ? c->UDF[par] : c->U16a[par];
         A.U.b[par] = c->U16b[par];
         A.C.p[par] = (sc.mode == M_FULL) ? c->C[p][par] : c->Ci[p][par];
     }
@@ -244,12 +244,13 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
         set_error_message("reduction grid too large");
         return QCD_EINVAL;
     }
-    ProfScope prof(c, p == QCD_F64 ? QCD_K_MULT_F64 : p == QCD_F32 ? QCD_K_MULT_F32 : QCD_K_MULT_F16,
+    ProfScope prof(c, p == QCD_F32 ? QCD_K_MULT_F32 : p == QCD_F16 ? QCD_K_MULT_F16 : QCD_K_MULT_F64,
                    stencil_bytes(c, sc));
     A.skip = prof.flag;
     int rc;
     if (p == QCD_F64) rc = dispatch<QCD_F64>(sc, A, grid, block, c->stream, variant);
     else if (p == QCD_F32) rc = dispatch<QCD_F32>(sc, A, grid, block, c->stream, variant);
+    else if (p == QCD_DF64) rc = dispatch<QCD_DF64>(sc, A, grid, block, c->stream, variant);
     else rc = dispatch<QCD_F16>(sc, A, grid, block, c->stream, variant);
     if (rc != QCD_OK) return rc;
     QCD_CUDA_CHECK(cudaGetLastError());

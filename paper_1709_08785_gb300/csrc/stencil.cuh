@@ -147,6 +147,147 @@ __device__ __forceinline__ void hopping(const Geom &g, const GaugePtr &U, const 
     hop_dir<P, 3, SF>(g, U, in, out_par, cb, lex, c, acc);
 }
 
+// ---- rolled forms ----------------------------------------------------------
+// For the double-float arithmetic each complex multiply-add is ~60 FP32
+// instructions; the fully unrolled stencil would not fit the instruction
+// cache and the SM would wait on instruction fetch.  These forms loop over
+// the 8 directions and the clover rows at run time instead.
+template <class T>
+__device__ __forceinline__ void project_rt(int mu, int s, const Spinor<T> &p, cx<T> h[2][3])
+{
+    switch (2 * mu + (s > 0 ? 0 : 1)) {
+    case 0: project<0, 1>(p, h); break;
+    case 1: project<0, -1>(p, h); break;
+    case 2: project<1, 1>(p, h); break;
+    case 3: project<1, -1>(p, h); break;
+    case 4: project<2, 1>(p, h); break;
+    case 5: project<2, -1>(p, h); break;
+    case 6: project<3, 1>(p, h); break;
+    default: project<3, -1>(p, h); break;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void expand_rt(int mu, int s, Spinor<T> &acc, const cx<T> g[2][3])
+{
+    switch (2 * mu + (s > 0 ? 0 : 1)) {
+    case 0: expand<0, 1>(acc, g); break;
+    case 1: expand<0, -1>(acc, g); break;
+    case 2: expand<1, 1>(acc, g); break;
+    case 3: expand<1, -1>(acc, g); break;
+    case 4: expand<2, 1>(acc, g); break;
+    case 5: expand<2, -1>(acc, g); break;
+    case 6: expand<3, 1>(acc, g); break;
+    default: expand<3, -1>(acc, g); break;
+    }
+}
+
+template <int P, bool DAG>
+__device__ void hopping_rolled(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par, int cb,
+                               Spinor<typename Prec<P>::T> &acc)
+{
+    using T = typename Prec<P>::T;
+    int c[4];
+    site_coords(g, out_par, cb, c);
+    const int lex = lex_of(g, c);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc.s[a][i] = mk(T(0), T(0));
+    constexpr int SF = DAG ? -1 : 1;
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        // forward: (1 - SF g_mu) U_mu(n) psi(n+mu); backward: (1 + SF g_mu) U_mu(n-mu)^dag psi(n-mu)
+        const int nb = lex_hop(g, lex, c, mu, fwd ? +1 : -1) >> 1;
+        const int s = fwd ? SF : -SF;
+        Spinor<T> psi;
+        Prec<P>::load(in, nb, psi);
+        cx<T> h[2][3], q[2][3];
+        project_rt(mu, s, psi, h);
+        Link<T> L;
+        Prec<P>::load_link(U, fwd ? out_par : 1 - out_par, fwd ? cb : nb, mu, L);
+        if (!fwd) {
+            Link<T> D;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) D.u[i][j] = conj(L.u[j][i]);
+            L = D;
+        }
+        colour_mul<false>(L, h, q);
+        if (mu == 3 && g.t_bc < 0 && (fwd ? c[3] == g.L[3] - 1 : c[3] == 0)) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) q[a][i] = -q[a][i];
+        }
+        expand_rt(mu, s, acc, q);
+    }
+}
+
+// y = A x for one Hermitian 6x6 block with rolled loops (see herm6)
+template <class T>
+__device__ void herm6_rolled(const T d[6], const cx<T> o[15], const cx<T> x[6], cx<T> y[6])
+{
+#pragma unroll 1
+    for (int i = 0; i < 6; ++i) {
+        cx<T> a = mk(d[i] * x[i].r, d[i] * x[i].i);
+#pragma unroll 1
+        for (int j = 0; j < 6; ++j) {
+            if (j < i) fma_(a, o[i * (i - 1) / 2 + j], x[j]);
+            else if (j > i) fmac_(a, o[j * (j - 1) / 2 + i], x[j]);
+        }
+        y[i] = a;
+    }
+}
+
+template <int P>
+__device__ void apply_clover_rolled(const CloverPtr &cl, int par, int cb, Spinor<typename Prec<P>::T> &s)
+{
+    using T = typename Prec<P>::T;
+    cx<T> x[2][6], y[2][6];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            x[0][3 * a + i] = s.s[a][i] - s.s[a + 2][i];
+            x[1][3 * a + i] = s.s[a][i] + s.s[a + 2][i];
+        }
+#pragma unroll 1
+    for (int blk = 0; blk < 2; ++blk) {
+        T d[6];
+        cx<T> o[15];
+        Prec<P>::load_clover(cl, par, cb, blk, d, o);
+        herm6_rolled(d, o, x[blk], y[blk]);
+    }
+    const T h = T(0.5);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            s.s[a][i] = h * (y[0][3 * a + i] + y[1][3 * a + i]);
+            s.s[a + 2][i] = h * (y[1][3 * a + i] - y[0][3 * a + i]);
+        }
+}
+
+// the forms each precision uses
+template <int P, bool DAG>
+__device__ __forceinline__ void hopping_any(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par, int cb,
+                                            Spinor<typename Prec<P>::T> &acc)
+{
+    if constexpr (P == QCD_DF64) hopping_rolled<P, DAG>(g, U, in, out_par, cb, acc);
+    else hopping<P, DAG>(g, U, in, out_par, cb, acc);
+}
+
+template <int P>
+__device__ __forceinline__ void clover_any(const CloverPtr &cl, int par, int cb, Spinor<typename Prec<P>::T> &s)
+{
+    if constexpr (P == QCD_DF64) apply_clover_rolled<P>(cl, par, cb, s);
+    else apply_clover<P>(cl, par, cb, s);
+}
+
 struct StencilArgs {
     Geom g;
     GaugePtr U;

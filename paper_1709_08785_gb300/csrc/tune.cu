@@ -138,7 +138,7 @@ int tune_one(qcd_ctx *c, StencilCall s, qcd_ctx::TuneEntry *out)
     s.norm_stride = (size_t)c->g.Vh_pad;
     s.red_args = RedArgs{c->partials, c->counters, c->states + ST_TUNE, FIN_NONE};
     s.done = nullptr;
-    const int nv = s.prec == QCD_F64 ? 1 : 2;
+    const int nv = (s.prec == QCD_F32 || s.prec == QCD_F16) ? 2 : 1;
     const int bxs1[] = {64, 128, 256}, bxsn[] = {32, 64};
     const int *bxs = s.nrhs > 1 ? bxsn : bxs1;
     const int nbx = s.nrhs > 1 ? 2 : 3;
@@ -176,6 +176,8 @@ int autotune(qcd_ctx *c, const char *cache_path)
         {QCD_F32, M_HOP, R_NONE, 1},   {QCD_F32, M_MULT, R_NONE, 12},
         {QCD_F16, M_MULT, R_NONE, 1},  {QCD_F16, M_DHAT, R_DOT_AUX, 1}, {QCD_F16, M_DHAT, R_OMEGA, 1},
         {QCD_F16, M_MULT, R_NONE, 12},
+        {QCD_DF64, M_MULT, R_NONE, 1}, {QCD_DF64, M_DHAT, R_DOT_AUX, 1}, {QCD_DF64, M_DHAT, R_OMEGA, 1},
+        {QCD_DF64, M_SRC, R_NONE, 1},  {QCD_DF64, M_DHAT, R_NORM, 1},
     };
     Cache cache = read_cache(cache_path);
     const std::string prefix = cache_prefix(c);

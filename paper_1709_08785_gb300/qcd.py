@@ -12,7 +12,7 @@ import ctypes
 import os
 from dataclasses import dataclass, field
 
-F64, F32, F16 = 0, 1, 2
+F64, F32, F16, DF64 = 0, 1, 2, 3
 K_MULT_F64, K_MULT_F32, K_MULT_F16, K_BLAS, K_OTHER = 0, 1, 2, 3, 4
 
 STATUS = {
@@ -37,6 +37,7 @@ class SolveOpts(ctypes.Structure):
         ("max_inner", ctypes.c_int * 2),
         ("max_restarts", ctypes.c_int),
         ("use_x0", ctypes.c_int),
+        ("outer_df64", ctypes.c_int),
     ]
 
 

@@ -16,7 +16,7 @@ from paper_1709_08785_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-13, 1: 2e-6, 2: 2e-3}
+TOL = {0: 1e-13, 1: 2e-6, 2: 2e-3, 3: 1e-13}  # 3: DF64 (float pairs, complex128 buffers)
 LATTICES = [
     # dims, t_bc, eps, kappa, csw
     ((4, 4, 4, 4), -1, 0.3, 0.12, 1.0),
@@ -46,7 +46,7 @@ def lat(request):
 
 
 def dev(a, prec):
-    dt = np.complex128 if prec == 0 else np.complex64
+    dt = np.complex128 if prec in (0, 3) else np.complex64
     return torch.from_numpy(np.ascontiguousarray(a.astype(dt))).cuda()
 
 
@@ -58,7 +58,7 @@ def run(fn, a, prec, nrhs=1):
     return out.cpu().numpy().astype(np.complex128)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("out_parity", [0, 1])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_dslash_eo(lat, prec, out_parity, dagger):
@@ -69,7 +69,7 @@ def test_dslash_eo(lat, prec, out_parity, dagger):
     assert rel(got, want) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("parity", [0, 1])
 @pytest.mark.parametrize("inverse", [False, True])
 def test_clover_apply(lat, prec, parity, inverse):
@@ -82,7 +82,7 @@ def test_clover_apply(lat, prec, parity, inverse):
     assert rel(got, want) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("out_parity", [0, 1])
 def test_mult(lat, prec, out_parity):
     dims = lat["dims"]
@@ -93,7 +93,7 @@ def test_mult(lat, prec, out_parity):
     assert rel(got, want) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_dhat(lat, prec):
     dims = lat["dims"]
     Vh = inputs.volume(dims) // 2
@@ -114,7 +114,7 @@ def test_dirac_full(lat):
     assert rel(out.cpu().numpy(), want) < TOL[0]
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("nrhs", [3, 12])
 def test_multi_rhs_matches_single(lat, prec, nrhs):
     """Each column of a multi-RHS launch equals the single-RHS result (bit

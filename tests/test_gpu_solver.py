@@ -91,6 +91,14 @@ def test_even_odd_solves_8c16(c2s, levels):
         assert info["dhat_applies"][2] > 0
 
 
+@pytest.mark.parametrize("levels", [2, 3])
+def test_fp64_outer_arithmetic(c2s, levels):
+    """The nested schemes with the outer level in FP64 instead of DF64."""
+    x, info = solve(c2s, precision_levels=levels, outer_df64=0)
+    assert info["status"] == 0, info
+    assert true_res(c2s, x) <= 1e-12
+
+
 def test_host_buffers(c1):
     x = np.zeros_like(c1["b"])
     info = c1["ctx"].solve(c1["b"], x, tol=1e-12, precision_levels=2)
