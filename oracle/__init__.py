@@ -126,6 +126,37 @@ def dirac_sites(dims, t_bc, U, kappa, csw, psi, sites):
     return out
 
 
+def hop_sites(dims, t_bc, U, psi, sites, dagger=False):
+    """(H psi)(n) at the listed lexicographic sites, [len(sites), 4, 3]."""
+    U, psi = _c(U), _c(psi)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+    lib().oracle_hop_sites(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(psi), ctypes.c_long(len(sites)), _p(sites),
+                           _p(out), ctypes.c_int(int(dagger)))
+    return out
+
+
+def clover_sites(dims, U, kappa, csw, sites):
+    """F(n) at the listed lexicographic sites, [len(sites), 12, 12]."""
+    U = _c(U)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    F = np.empty((len(sites), 12, 12), dtype=np.complex128)
+    lib().oracle_clover_sites(_dims(dims), _p(U), ctypes.c_double(kappa), ctypes.c_double(csw),
+                              ctypes.c_long(len(sites)), _p(sites), _p(F))
+    return F
+
+
+def site_of_cb(dims, parity, cb):
+    """Lexicographic index of the cb-th site of a parity (cb = lex/2)."""
+    cb = np.asarray(cb, dtype=np.int64)
+    s = 2 * cb
+    Lx, Ly, Lz = int(dims[0]), int(dims[1]), int(dims[2])
+    x, r = s % Lx, s // Lx
+    y, r = r % Ly, r // Ly
+    z, t = r % Lz, r // Lz
+    return np.where((x + y + z + t) % 2 == parity, s, s + 1)
+
+
 # ---------------------------------------------------------------- even-odd
 def half_to_full(dims, parity, half):
     half = _c(half)

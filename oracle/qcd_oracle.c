@@ -438,6 +438,29 @@ void oracle_dirac_sites(const int L[4], int t_bc, const double *U_, double kappa
     }
 }
 
+/* (H psi)(n) at a list of sites only (psi a full-lattice vector) */
+void oracle_hop_sites(const int L[4], int t_bc, const double *U_, const double *in_, long nsamp, const long *sites,
+                      double *out_, int dagger)
+{
+    cplx g[5][4][4];
+    build_gammas(g);
+    const cplx *U = (const cplx *)U_;
+    const cplx *in = (const cplx *)in_;
+    cplx *out = (cplx *)out_;
+    for (long k = 0; k < nsamp; ++k) hop_site(L, t_bc, U, in, sites[k], g, dagger, out + k * 12);
+}
+
+/* F(n) as 12x12 matrices at a list of sites only */
+void oracle_clover_sites(const int L[4], const double *U_, double kappa, double csw, long nsamp, const long *sites,
+                         double *F_)
+{
+    cplx g[5][4][4];
+    build_gammas(g);
+    const cplx *U = (const cplx *)U_;
+    cplx *F = (cplx *)F_;
+    for (long k = 0; k < nsamp; ++k) clover_site(L, U, sites[k], kappa, csw, g, F + k * 144);
+}
+
 /* ------------------------------------------------------------------ */
 /* even-odd pieces, Eqs. (5)-(9)                                       */
 /* ------------------------------------------------------------------ */

@@ -332,6 +332,25 @@ def test_nested_bicgstab_matches_dense_solve(c1_problem):
     assert rel(x, P["xd"]) < 1e-10
 
 
+# ------------------------------------------------------------- sampled sites
+def test_sampled_site_helpers_match_the_full_lattice():
+    """The per-site entry points used for the full-size checks agree with the
+    full-lattice functions (same definitions, evaluated at chosen sites)."""
+    dims, t_bc, kappa, csw = (4, 2, 4, 6), -1, 0.12, 1.3
+    U = inputs.random_gauge(dims, 0.3, 40)
+    psi = inputs.gaussian_source(dims, 41)
+    sites = np.array([0, 5, 17, 63, 95, 191])
+    assert np.array_equal(oracle.hop_sites(dims, t_bc, U, psi, sites), oracle.hopping(dims, t_bc, U, psi)[sites])
+    F = oracle.clover_field(dims, U, kappa, csw)
+    assert np.array_equal(oracle.clover_sites(dims, U, kappa, csw, sites), F[sites])
+    Dx = oracle.dirac(dims, t_bc, U, F, kappa, psi)
+    assert np.max(np.abs(oracle.dirac_sites(dims, t_bc, U, kappa, csw, psi, sites) - Dx[sites])) < 1e-13
+    for par in (0, 1):
+        half = oracle.full_to_half(dims, par, psi)
+        cbs = np.arange(inputs.volume(dims) // 2)
+        assert np.array_equal(psi[oracle.site_of_cb(dims, par, cbs)], half)
+
+
 # ------------------------------------------------------------- P12 gradient
 def test_link_gradient_finite_differences():
     """dF/dh along U_l -> exp(i h T) U_l, by central differences of the
