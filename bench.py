@@ -119,6 +119,18 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The maximum of a per-rank time over all ranks (the replicas' timed
+    region ends when the slowest rank ends); the value itself with one rank."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------------- oracle
 def oracle_sample(dims, U, b, W, reps):
     """Time `reps` oracle D^ applications (one core) on the full lattice."""
@@ -242,10 +254,7 @@ def run_ours(args):
     st32 = ctx.kernel_stats(qcd.K_MULT_F32)
     st64 = ctx.kernel_stats(qcd.K_MULT_F64)
     stbl = ctx.kernel_stats(qcd.K_BLAS)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, "cuda")
     ms_step = ms_total / args.steps
     mixed = infos[-1]
 

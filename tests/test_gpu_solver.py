@@ -131,6 +131,24 @@ def test_nonfinite_source(c1):
     assert info["rc"] == -6  # QCD_ENONFINITE
 
 
+def test_singular_clover_block_reported(c1):
+    """A clover block whose LDL^H pivots are not finite (one NaN link) is
+    reported as QCD_ECLOVER_SINGULAR; a good field afterwards builds again."""
+    qcd = c1["qcd"]
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, 0.3, 1)
+    bad = U.copy()
+    bad[17, 2, 0, 1] = np.nan
+    ctx = qcd.Context(dims)
+    ctx.gauge_load(torch.from_numpy(bad).cuda())
+    with pytest.raises(qcd.QCDError) as e:
+        ctx.clover_build(0.12, 1.0)
+    assert e.value.status == -7
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(0.12, 1.0)
+    ctx.close()
+
+
 def test_iteration_cap(c1):
     bd = torch.from_numpy(c1["b"]).cuda()
     x = torch.zeros_like(bd)
