@@ -289,13 +289,25 @@ int qcd_tune_info(qcd_ctx *ctx, int max, unsigned *keys, int *variant, int *thre
 /* Time the fused MULT kernel (Sec. II-B, out = F^-1 H_{p,1-p} in) alone on
  * internal, already-resident buffers: `iters` launches on nrhs right-hand
  * sides (nrhs <= 16) in precision prec, each launch bracketed by CUDA
- * events and preceded by a write of 256 MB that evicts L2.  Returns the
- * mean device time of one launch and its algorithmic bytes (each input
- * read once, the output written once).  Synchronous.  Needs the clover
- * term.  Allocates two nrhs-vector buffers and the flush buffer on first
- * use. */
+ * events and preceded by a read of a 256 MB buffer that evicts L2 (clean
+ * lines replace the cache contents, so no write-back of earlier kernels'
+ * data falls inside the timed launch).  Returns the mean device time of one
+ * launch and its algorithmic bytes (each input read once, the output
+ * written once).  Synchronous.  Needs the clover term (QCD_ESTATE);
+ * QCD_EINVAL for a NULL output pointer, prec outside 0..3, nrhs outside
+ * 1..16 or iters < 1.  Allocates two nrhs-vector buffers and the flush
+ * buffer on first use. */
 int qcd_mult_benchmark(qcd_ctx *ctx, int prec, int nrhs, int iters, double *ms_per_launch,
                        double *bytes_per_launch);
+
+/* As qcd_mult_benchmark, but `iters` launches back to back with one pair of
+ * CUDA events around all of them and no eviction in between: the rate of a
+ * stream of MULTs, as inside a solver (the input vector stays in L2 from one
+ * launch to the next; the links and clover, larger than L2 at production
+ * sizes, stream from HBM).  Returns the mean time of one launch, launch
+ * gaps included, and its algorithmic bytes.  Same arguments and errors. */
+int qcd_mult_throughput(qcd_ctx *ctx, int prec, int nrhs, int iters, double *ms_per_launch,
+                        double *bytes_per_launch);
 
 const char *qcd_strerror(int status);
 const char *qcd_last_error(void);

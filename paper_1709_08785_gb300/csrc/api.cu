@@ -683,18 +683,26 @@ extern "C" int qcd_tune_info(qcd_ctx *c, int max, unsigned *keys, int *variant, 
     return tune_entries(c, max, keys, variant, threads, us);
 }
 
-extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, double *ms_per_launch,
-                                  double *bytes_per_launch)
+namespace {
+
+// Reads every line of the flush buffer once (clean lines replace whatever L2
+// held; dirty lines of earlier kernels are written back here, not inside the
+// timed launch).  The sink is written only if the sum equals a value the
+// buffer never produces, which keeps the loads.
+__global__ void k_l2_evict(const uint4 *__restrict__ buf, size_t n, unsigned *sink)
 {
-    if (!c || !ms_per_launch || !bytes_per_launch || prec < QCD_F64 || prec > QCD_DF64 || nrhs < 1 || nrhs > 16 ||
-        iters < 1) {
-        set_error_message("invalid benchmark arguments");
-        return QCD_EINVAL;
+    unsigned acc = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldcs(buf + i);
+        acc += v.x ^ v.y ^ v.z ^ v.w;
     }
-    if (!c->have_clover) {
-        set_error_message("qcd_mult_benchmark needs the clover term");
-        return QCD_ESTATE;
-    }
+    if (acc == 0x9e3779b9u) *sink = acc;
+}
+
+// The benchmark buffers: nrhs input and output vectors in precision prec,
+// the input filled with a fixed pattern.
+int bench_buffers(qcd_ctx *c, int prec, int nrhs, StencilCall &s)
+{
     const size_t hb = hvec_bytes(c->g, prec);
     const size_t nb = (size_t)c->g.Vh_pad * sizeof(float);
     const size_t need = 2 * nrhs * (hb + nb);
@@ -711,8 +719,6 @@ extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, dou
         if ((rc = dev_alloc(c, &c->bench_buf, need))) return rc;
         c->bench_bytes = need;
     }
-    const size_t flush_bytes = 256u << 20;
-    if (!c->flush_buf && (rc = dev_alloc(c, &c->flush_buf, flush_bytes))) return rc;
     char *base = (char *)c->bench_buf;
     HVec in, out;
     in.prec = out.prec = prec;
@@ -722,7 +728,6 @@ extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, dou
     out.norm = (float *)(base + 2 * nrhs * hb + nrhs * nb);
     const size_t stride = hvec_elems(c->g, prec);
     if ((rc = fill_pattern(c, prec, in, nrhs, stride, 7))) return rc;
-    StencilCall s;
     s.prec = prec;
     s.mode = M_MULT;
     s.out_par = 0;
@@ -731,12 +736,45 @@ extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, dou
     s.nrhs = nrhs;
     s.rhs_stride = stride;
     s.norm_stride = (size_t)c->g.Vh_pad;
+    return QCD_OK;
+}
+
+int bench_check(qcd_ctx *c, int prec, int nrhs, int iters, const void *a, const void *b)
+{
+    if (!c || !a || !b || prec < QCD_F64 || prec > QCD_DF64 || nrhs < 1 || nrhs > 16 || iters < 1) {
+        set_error_message("invalid benchmark arguments");
+        return QCD_EINVAL;
+    }
+    if (!c->have_clover) {
+        set_error_message("the MULT benchmarks need the clover term");
+        return QCD_ESTATE;
+    }
+    return QCD_OK;
+}
+
+}  // namespace
+
+extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, double *ms_per_launch,
+                                  double *bytes_per_launch)
+{
+    int rc;
+    if ((rc = bench_check(c, prec, nrhs, iters, ms_per_launch, bytes_per_launch))) return rc;
+    StencilCall s;
+    if ((rc = bench_buffers(c, prec, nrhs, s))) return rc;
+    const size_t flush_bytes = 256u << 20;
+    if (!c->flush_buf) {
+        if ((rc = dev_alloc(c, &c->flush_buf, flush_bytes + 256))) return rc;
+        QCD_CUDA_CHECK(cudaMemsetAsync(c->flush_buf, 0x5a, flush_bytes + 256, c->stream));
+    }
+    const uint4 *fb = (const uint4 *)c->flush_buf;
+    unsigned *sink = (unsigned *)((char *)c->flush_buf + flush_bytes);
     cudaEvent_t e0, e1;
     QCD_CUDA_CHECK(cudaEventCreate(&e0));
     QCD_CUDA_CHECK(cudaEventCreate(&e1));
     double total = 0.0;
     for (int it = -2; it < iters; ++it) {  // two untimed warm-up launches
-        QCD_CUDA_CHECK(cudaMemsetAsync(c->flush_buf, it & 0xff, flush_bytes, c->stream));
+        k_l2_evict<<<c->num_sms * 8, 256, 0, c->stream>>>(fb, flush_bytes / sizeof(uint4), sink);
+        QCD_CUDA_CHECK(cudaGetLastError());
         QCD_CUDA_CHECK(cudaEventRecord(e0, c->stream));
         if ((rc = launch_stencil(c, s))) break;
         QCD_CUDA_CHECK(cudaEventRecord(e1, c->stream));
@@ -749,6 +787,33 @@ extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, dou
     cudaEventDestroy(e1);
     if (rc) return rc;
     *ms_per_launch = total / iters;
+    *bytes_per_launch = stencil_bytes(c, s);
+    return QCD_OK;
+}
+
+extern "C" int qcd_mult_throughput(qcd_ctx *c, int prec, int nrhs, int iters, double *ms_per_launch,
+                                   double *bytes_per_launch)
+{
+    int rc;
+    if ((rc = bench_check(c, prec, nrhs, iters, ms_per_launch, bytes_per_launch))) return rc;
+    StencilCall s;
+    if ((rc = bench_buffers(c, prec, nrhs, s))) return rc;
+    cudaEvent_t e0, e1;
+    QCD_CUDA_CHECK(cudaEventCreate(&e0));
+    QCD_CUDA_CHECK(cudaEventCreate(&e1));
+    for (int it = 0; it < 2 && !rc; ++it) rc = launch_stencil(c, s);  // warm-up
+    if (!rc) QCD_CUDA_CHECK(cudaEventRecord(e0, c->stream));
+    for (int it = 0; it < iters && !rc; ++it) rc = launch_stencil(c, s);
+    float ms = 0.f;
+    if (!rc) {
+        QCD_CUDA_CHECK(cudaEventRecord(e1, c->stream));
+        QCD_CUDA_CHECK(cudaEventSynchronize(e1));
+        QCD_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    *ms_per_launch = ms / iters;
     *bytes_per_launch = stencil_bytes(c, s);
     return QCD_OK;
 }

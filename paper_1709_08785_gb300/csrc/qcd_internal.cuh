@@ -38,6 +38,41 @@ constexpr int SB = 32;  // sites per block of the site-blocked layout
 
 __host__ __device__ inline long pad_sites(long n) { return (n + SB - 1) / SB * SB; }
 
+// Loads of data that one kernel reads exactly once (the links and the clover
+// blocks of a MULT: every link joins one site of each parity): no L1
+// allocation and an L2 evict-first policy, so the vectors the solver writes
+// and reads back in consecutive kernels keep their L2 lines.
+#define QCD_LD_STREAM(VEC, REGS, ...)                                            \
+    asm("{\n\t.reg .b64 pol;\n\t"                                               \
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"              \
+        "ld.global.nc.L1::no_allocate.L2::cache_hint." VEC " " REGS ", pol;\n\t}" \
+        : __VA_ARGS__)
+__device__ __forceinline__ float4 ld_stream(const float4 *p)
+{
+    float4 v;
+    QCD_LD_STREAM("v4.f32", "{%0, %1, %2, %3}, [%4]", "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2 *p)
+{
+    double2 v;
+    QCD_LD_STREAM("v2.f64", "{%0, %1}, [%2]", "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p)
+{
+    uint4 v;
+    QCD_LD_STREAM("v4.u32", "{%0, %1, %2, %3}, [%4]", "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2 *p)
+{
+    uint2 v;
+    QCD_LD_STREAM("v2.u32", "{%0, %1}, [%2]", "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+#undef QCD_LD_STREAM
+
 struct Geom {
     int L[4];
     int Lxh;      // Lx / 2
@@ -237,7 +272,7 @@ struct Prec<QCD_F64> {
         const double2 *p = (const double2 *)g.a[par];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            double2 d = __ldg(p + soa(cb, 36, mu * 9 + k));
+            double2 d = ld_stream(p + soa(cb, 36, mu * 9 + k));
             U.u[k / 3][k % 3] = mk(d.x, d.y);
         }
     }
@@ -248,13 +283,13 @@ struct Prec<QCD_F64> {
         const int k0 = blk * 18;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double2 v = __ldg(p + soa(cb, 36, k0 + k));
+            double2 v = ld_stream(p + soa(cb, 36, k0 + k));
             d[2 * k] = v.x;
             d[2 * k + 1] = v.y;
         }
 #pragma unroll
         for (int k = 0; k < 15; ++k) {
-            double2 v = __ldg(p + soa(cb, 36, k0 + 3 + k));
+            double2 v = ld_stream(p + soa(cb, 36, k0 + 3 + k));
             o[k] = mk(v.x, v.y);
         }
     }
@@ -297,9 +332,9 @@ struct Prec<QCD_F32> {
     static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
     {
         const float4 *p = (const float4 *)g.a[par];
-        float4 f0 = __ldg(p + soa(cb, 12, mu * 3 + 0));
-        float4 f1 = __ldg(p + soa(cb, 12, mu * 3 + 1));
-        float4 f2 = __ldg(p + soa(cb, 12, mu * 3 + 2));
+        float4 f0 = ld_stream(p + soa(cb, 12, mu * 3 + 0));
+        float4 f1 = ld_stream(p + soa(cb, 12, mu * 3 + 1));
+        float4 f2 = ld_stream(p + soa(cb, 12, mu * 3 + 2));
         U.u[0][0] = mk(f0.x, f0.y);
         U.u[1][0] = mk(f0.z, f0.w);
         U.u[2][0] = mk(f1.x, f1.y);
@@ -314,7 +349,7 @@ struct Prec<QCD_F32> {
         float r[36];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            float4 f = __ldg(p + soa(cb, 18, blk * 9 + k));
+            float4 f = ld_stream(p + soa(cb, 18, blk * 9 + k));
             r[4 * k] = f.x;
             r[4 * k + 1] = f.y;
             r[4 * k + 2] = f.z;
@@ -377,8 +412,8 @@ struct Prec<QCD_F16> {
     }
     static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
     {
-        uint4 qa = __ldg((const uint4 *)g.a[par] + soa(cb, 4, mu));
-        uint2 qb = __ldg((const uint2 *)g.b[par] + soa(cb, 4, mu));
+        uint4 qa = ld_stream((const uint4 *)g.a[par] + soa(cb, 4, mu));
+        uint2 qb = ld_stream((const uint2 *)g.b[par] + soa(cb, 4, mu));
         U.u[0][0] = h2c(u2h(qa.x));
         U.u[1][0] = h2c(u2h(qa.y));
         U.u[2][0] = h2c(u2h(qa.z));
@@ -397,7 +432,7 @@ struct Prec<QCD_F16> {
         for (int k = 0; k < 9; ++k) {
             if (blk == 0 && k > 4) continue;
             if (blk == 1 && k < 4) continue;
-            uint4 q = __ldg(p + soa(cb, 9, k));
+            uint4 q = ld_stream(p + soa(cb, 9, k));
             unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -441,7 +476,7 @@ struct Prec<QCD_DF64> {
     {
         const float4 *p = (const float4 *)g.a[par];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) U.u[k / 3][k % 3] = f4c(__ldg(p + soa(cb, 36, mu * 9 + k)));
+        for (int k = 0; k < 9; ++k) U.u[k / 3][k % 3] = f4c(ld_stream(p + soa(cb, 36, mu * 9 + k)));
     }
     static __device__ __forceinline__ void load_clover(const CloverPtr &c, int par, int cb, int blk, T d[6], cx<T> o[15])
     {
@@ -449,12 +484,12 @@ struct Prec<QCD_DF64> {
         const int k0 = blk * 18;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float4 v = __ldg(p + soa(cb, 36, k0 + k));
+            const float4 v = ld_stream(p + soa(cb, 36, k0 + k));
             d[2 * k] = df(v.x, v.y);
             d[2 * k + 1] = df(v.z, v.w);
         }
 #pragma unroll
-        for (int k = 0; k < 15; ++k) o[k] = f4c(__ldg(p + soa(cb, 36, k0 + 3 + k)));
+        for (int k = 0; k < 15; ++k) o[k] = f4c(ld_stream(p + soa(cb, 36, k0 + 3 + k)));
     }
 };
 

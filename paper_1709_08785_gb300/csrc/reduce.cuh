@@ -161,7 +161,22 @@ __device__ __forceinline__ void grid_reduce(double v[N], const RedArgs &ra)
     double s[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) s[k] = 0.0;
-    for (int b = tid; b < (int)gridDim.x; b += nthr)
+    // eight independent loads in flight per thread: the partials are read in
+    // a few L2 round trips instead of one per grid-stride step
+    const int G = (int)gridDim.x;
+    int b = tid;
+    for (; b + 7 * nthr < G; b += 8 * nthr) {
+        double t[8][N];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int k = 0; k < N; ++k) t[u][k] = __ldcg(ra.partials + (size_t)(b + u * nthr) * 4 + k);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int k = 0; k < N; ++k) s[k] += t[u][k];
+    }
+    for (; b < G; b += nthr)
 #pragma unroll
         for (int k = 0; k < N; ++k) s[k] += __ldcg(ra.partials + (size_t)b * 4 + k);
 #pragma unroll

@@ -202,7 +202,7 @@ __device__ __forceinline__ void mrhs_body(const StencilArgs &A)
         const float4 *Cl = (const float4 *)A.C.p[A.out_par];
         for (int k = tid; k < 18 * SB; k += nthr) {
             const int l = k & (SB - 1), comp = k >> 5;
-            s_clv[k] = (cb0 + l < A.g.Vh) ? __ldg(Cl + soa(cb0 + l, 18, comp)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            s_clv[k] = (cb0 + l < A.g.Vh) ? ld_stream(Cl + soa(cb0 + l, 18, comp)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     __syncthreads();

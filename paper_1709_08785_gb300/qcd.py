@@ -66,8 +66,9 @@ EXPORTS = [
     "qcd_create", "qcd_destroy", "qcd_set_stream", "qcd_gauge_load", "qcd_clover_build", "qcd_dslash_eo",
     "qcd_clover_apply", "qcd_mult_eo", "qcd_dhat", "qcd_dirac", "qcd_solve_opts_default", "qcd_solve",
     "qcd_set_profiling", "qcd_kernel_stats", "qcd_reset_kernel_stats", "qcd_strerror", "qcd_last_error",
-    "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_dslash_eo_noalloc", "qcd_solve_adjoint",
-    "qcd_force", "qcd_autotune", "qcd_tune_info", "qcd_solve_batched", "qcd_set_wait_limit", "qcd_set_graphs",
+    "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_mult_throughput", "qcd_dslash_eo_noalloc",
+    "qcd_solve_adjoint", "qcd_force", "qcd_autotune", "qcd_tune_info", "qcd_solve_batched", "qcd_set_wait_limit",
+    "qcd_set_graphs",
 ]
 
 _lib = None
@@ -117,6 +118,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.qcd_launch_count.restype = ctypes.c_long
     lib.qcd_dslash_eo_noalloc.argtypes = [vp, vp, vp, ip, ip, ip]
     lib.qcd_mult_benchmark.argtypes = [vp, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
+    lib.qcd_mult_throughput.argtypes = [vp, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)]
     lib.qcd_solve_adjoint.argtypes = [vp, vp, vp, dp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
     lib.qcd_force.argtypes = [vp, vp, vp, vp, vp]
     lib.qcd_solve_batched.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -321,4 +323,11 @@ class Context:
         ms, by = ctypes.c_double(0), ctypes.c_double(0)
         _check(self.lib.qcd_mult_benchmark(self._h, int(prec), int(nrhs), int(iters), ctypes.byref(ms),
                                            ctypes.byref(by)))
+        return dict(ms=ms.value, bytes=by.value, gbs=by.value / (ms.value * 1e-3) / 1e9)
+
+    def mult_throughput(self, prec: int = F32, nrhs: int = 1, iters: int = 100) -> dict:
+        """Back-to-back MULT launches without cache eviction (qcd.h)."""
+        ms, by = ctypes.c_double(0), ctypes.c_double(0)
+        _check(self.lib.qcd_mult_throughput(self._h, int(prec), int(nrhs), int(iters), ctypes.byref(ms),
+                                            ctypes.byref(by)))
         return dict(ms=ms.value, bytes=by.value, gbs=by.value / (ms.value * 1e-3) / 1e9)
