@@ -250,12 +250,14 @@ int qcd_force(qcd_ctx *ctx, const void *U, const void *x, const void *lam, void 
  * (and of the other solver kernels) is bracketed by CUDA events on the
  * context stream; qcd_kernel_stats sums them. */
 typedef enum {
-    QCD_K_MULT_F64 = 0,  /* MULT / D^ stencil kernels, by precision */
-    QCD_K_MULT_F32 = 1,
+    QCD_K_MULT_F64 = 0,  /* stencil kernels (MULT, D^, b^, x_o, D), by precision; */
+    QCD_K_MULT_F32 = 1,  /* FP32: all but the second half of D^, which is QCD_K_DHAT_F32 */
     QCD_K_MULT_F16 = 2,
     QCD_K_BLAS = 3,      /* fused BLAS-1 + reduction kernels */
     QCD_K_OTHER = 4,
-    QCD_K_COUNT = 5
+    QCD_K_DHAT_F32 = 5,  /* FP32 second half of D^ with its fused update and dot products */
+    QCD_K_MULT_DF64 = 6, /* DF64 stencil kernels */
+    QCD_K_COUNT = 7
 } qcd_kernel_class;
 
 typedef struct {

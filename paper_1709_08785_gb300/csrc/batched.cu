@@ -104,9 +104,11 @@ __device__ __forceinline__ int find_prob(const BatchArgs &A, int tile)
     return lo;
 }
 
-// block-level sum of N doubles into thread 0's v
-template <int N>
-__device__ __forceinline__ void block_sum(double v[N])
+// block-level sum of N values into thread 0's out: the warp stage in the
+// accumulator type A (float in the FP32 phases, see grid_reduce), the warp
+// sums in FP64
+template <int N, class A>
+__device__ __forceinline__ void block_sum(A v[N], double out[N])
 {
     __shared__ double sh[TILE / 32][4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -116,13 +118,13 @@ __device__ __forceinline__ void block_sum(double v[N])
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < N; ++k) sh[wid][k] = v[k];
+        for (int k = 0; k < N; ++k) sh[wid][k] = (double)v[k];
     __syncthreads();
     if (threadIdx.x == 0)
         for (int k = 0; k < N; ++k) {
             double t = 0.0;
             for (int w = 0; w < TILE / 32; ++w) t += sh[w][k];
-            v[k] = t;
+            out[k] = t;
         }
     __syncthreads();
 }
@@ -156,7 +158,9 @@ __device__ void run_phase(const BatchArgs &A, int ph)
         const bool in_range = cb < pr.g.Vh_pad;
         const bool site = cb < pr.g.Vh;
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        float accf[4] = {0.f, 0.f, 0.f, 0.f};  // the FP32 phases' sums
         int nred = 0;
+        bool f32red = false;
         switch (ph) {
         case PH_INIT: {  // b = src/|src|, r = r~ = p = b, x = 0 (src: p or r of the outer level)
             const SpinorPtr src = A.half == 0 ? pr.P : pr.R;
@@ -186,24 +190,27 @@ __device__ void run_phase(const BatchArgs &A, int ph)
                 if (ph == PH_DHAT_Q) {
                     Spinor<float> w;
                     Prec<C32>::load(pr.rt, cb, w);
-                    dot_sp(w, a, acc[0], acc[1]);
+                    acc_dot(w, a, accf[0], accf[1]);
                 } else {
-                    dot_sp(a, y, acc[0], acc[1]);
-                    acc[2] += norm2_sp(a);
+                    acc_dot(a, y, accf[0], accf[1]);
+                    acc_norm2(accf[2], a);
                 }
             }
             nred = 3;
+            f32red = true;
             break;
         case PH_S:
-            if (in_range) OpS<C32>{pr.r, pr.q, &s_in}(cb, acc);
+            if (in_range) OpS<C32>{pr.r, pr.q, &s_in}(cb, accf);
             nred = 1;
+            f32red = true;
             break;
         case PH_X:
-            if (in_range) OpX<C32>{pr.x, pr.p, pr.r, pr.t, pr.rt, &s_in}(cb, acc);
+            if (in_range) OpX<C32>{pr.x, pr.p, pr.r, pr.t, pr.rt, &s_in}(cb, accf);
             nred = 3;
+            f32red = true;
             break;
         case PH_P:
-            if (in_range) OpP<C32>{pr.p, pr.r, pr.q, &s_in}(cb, acc);
+            if (in_range) OpP<C32>{pr.p, pr.r, pr.q, &s_in}(cb, accf);
             break;
         case PH_LIFT:  // finish the inner solve: x += alpha p after a first-half exit; v = |src| x
             if (in_range) {
@@ -254,7 +261,8 @@ __device__ void run_phase(const BatchArgs &A, int ph)
             break;
         }
         if (nred) {
-            block_sum<3>(acc);
+            if (f32red) block_sum<3>(accf, acc);
+            else block_sum<3>(acc, acc);
             if (threadIdx.x == 0)
                 for (int k = 0; k < 4; ++k) pr.partials[(size_t)lt * 4 + k] = k < 3 ? acc[k] : 0.0;
         }

@@ -17,13 +17,15 @@ namespace qcd {
 template <int NRED, class Op>
 __global__ void __launch_bounds__(256) blas_kernel(int n, Op op, RedArgs red, const int *done, int *skip)
 {
+    pdl_enter();
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     if (done && *done) {
         if (skip && lead) *skip = 1;
         return;
     }
     if (skip && lead) *skip = 0;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    using A = typename AccOf<Op>::type;
+    A acc[4] = {A(0), A(0), A(0), A(0)};
     for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < n; cb += gridDim.x * blockDim.x) op(cb, acc);
     if constexpr (NRED > 0) grid_reduce<NRED>(acc, red);
 }
@@ -42,7 +44,7 @@ static int run(qcd_ctx *c, int nsites, const Op &op, int fin, SolverState *st, c
     ra.st = st;
     ra.op = fin;
     ProfScope prof(c, cls, bytes);
-    blas_kernel<NRED><<<blocks, threads, 0, c->stream>>>(nsites, op, ra, done, prof.flag);
+    launch_pdl(blas_kernel<NRED, Op>, dim3(blocks), dim3(threads), 0, c->stream, nsites, op, ra, done, prof.flag);
     QCD_CUDA_CHECK(cudaGetLastError());
     return QCD_OK;
 }

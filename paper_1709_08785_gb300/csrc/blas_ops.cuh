@@ -3,6 +3,8 @@
 // blas.cu and the batched persistent solver.
 #pragma once
 
+#include <type_traits>
+
 #include "reduce.cuh"
 
 namespace qcd {
@@ -34,6 +36,47 @@ __device__ __forceinline__ void dot_sp(const Spinor<T> &a, const Spinor<T> &b, d
     re += (double)r;
     im += (double)i;
 }
+
+// Accumulation into the reduction type A of a kernel (float at the FP32 and
+// FP16 levels, double otherwise): the site's sum is formed in the spinor's
+// arithmetic type T and converted once (acc_cast).
+template <class A, class T>
+__device__ __forceinline__ void acc_norm2(A &acc, const Spinor<T> &a)
+{
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s += a.s[k][i].r * a.s[k][i].r + a.s[k][i].i * a.s[k][i].i;
+    acc += acc_cast<A>(s);
+}
+
+// re + i im += <a|b> = sum conj(a) b
+template <class A, class T>
+__device__ __forceinline__ void acc_dot(const Spinor<T> &a, const Spinor<T> &b, A &re, A &im)
+{
+    T r = 0, i = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            r += a.s[k][c].r * b.s[k][c].r + a.s[k][c].i * b.s[k][c].i;
+            i += a.s[k][c].r * b.s[k][c].i - a.s[k][c].i * b.s[k][c].r;
+        }
+    re += acc_cast<A>(r);
+    im += acc_cast<A>(i);
+}
+
+// The reduction type of a BLAS functor: float for single-precision-level
+// functors (OpX<QCD_F32> and the like), double for every other one.
+template <class Op>
+struct AccOf {
+    using type = double;
+};
+template <template <int> class O, int P>
+struct AccOf<O<P>> {
+    using type = typename std::conditional<P == QCD_F32 || P == QCD_F16, float, double>::type;
+};
 
 // y += a x (complex a)
 template <class T>
@@ -84,7 +127,8 @@ template <int P>
 struct OpS {
     SpinorPtr r, q;
     const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> R, Q;
@@ -92,7 +136,7 @@ struct OpS {
         Prec<P>::load(q, cb, Q);
         caxpy(R, scal<T>(st->alpha, -1.0), Q);
         Prec<P>::store(r, cb, R);
-        acc[0] += norm2_sp(R);
+        acc_norm2(acc[0], R);
     }
 };
 
@@ -101,7 +145,8 @@ template <int P>
 struct OpX {
     SpinorPtr x, p, r, t, rt;
     const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> X, Pp, R, Tt, Rt;
@@ -115,8 +160,8 @@ struct OpX {
         caxpy(R, scal<T>(st->omega, -1.0), Tt);
         Prec<P>::store(r, cb, R);
         Prec<P>::load(rt, cb, Rt);
-        acc[0] += norm2_sp(R);
-        dot_sp(Rt, R, acc[1], acc[2]);
+        acc_norm2(acc[0], R);
+        acc_dot(Rt, R, acc[1], acc[2]);
     }
 };
 
@@ -125,7 +170,8 @@ template <int P>
 struct OpP {
     SpinorPtr p, r, q;
     const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> Pp, R, Q;
@@ -140,7 +186,7 @@ struct OpP {
 #pragma unroll
             for (int c = 0; c < 3; ++c) fma_(O.s[k][c], b, Pp.s[k][c]);
         Prec<P>::store(p, cb, O);
-        acc[0] += norm2_sp(O);
+        acc_norm2(acc[0], O);
     }
 };
 
@@ -149,7 +195,8 @@ template <int P>
 struct OpHalf {
     SpinorPtr x, p;
     const SolverState *st;
-    __device__ void operator()(int cb, double *) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *) const
     {
         using T = typename Prec<P>::T;
         if (!st->exit_half) return;
@@ -166,7 +213,8 @@ template <int P>
 struct OpFlex1 {
     SpinorPtr x, v, r, q;
     const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> X, V, R, Q;
@@ -178,7 +226,7 @@ struct OpFlex1 {
         Prec<P>::load(q, cb, Q);
         caxpy(R, scal<T>(st->alpha, -1.0), Q);
         Prec<P>::store(r, cb, R);
-        acc[0] += norm2_sp(R);
+        acc_norm2(acc[0], R);
     }
 };
 
@@ -187,7 +235,8 @@ template <int P>
 struct OpFlex2 {
     SpinorPtr x, v, r, t, rt;
     const SolverState *st;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> X, V, R, Tt, Rt;
@@ -200,8 +249,8 @@ struct OpFlex2 {
         caxpy(R, scal<T>(st->omega, -1.0), Tt);
         Prec<P>::store(r, cb, R);
         Prec<P>::load(rt, cb, Rt);
-        acc[0] += norm2_sp(R);
-        dot_sp(Rt, R, acc[1], acc[2]);
+        acc_norm2(acc[0], R);
+        acc_dot(Rt, R, acc[1], acc[2]);
     }
 };
 
@@ -210,7 +259,8 @@ template <int P>
 struct OpInit {
     SpinorPtr src, r, rt, p, x;
     int zero_x;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> S;
@@ -223,7 +273,7 @@ struct OpInit {
             zero_sp(Z);
             Prec<P>::store(x, cb, Z);
         }
-        acc[0] += norm2_sp(S);
+        acc_norm2(acc[0], S);
     }
 };
 
@@ -233,7 +283,8 @@ template <int PS, int PD>
 struct OpInner {
     SpinorPtr src, r, rt, p, x;
     const double *src_norm2;
-    __device__ void operator()(int cb, double *) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *) const
     {
         using TS = typename Prec<PS>::T;
         using TD = typename Prec<PD>::T;
@@ -258,7 +309,8 @@ template <int PS, int PD>
 struct OpLift {
     SpinorPtr x, v;
     const double *src_norm2;
-    __device__ void operator()(int cb, double *) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *) const
     {
         using TS = typename Prec<PS>::T;
         using TD = typename Prec<PD>::T;
@@ -274,12 +326,13 @@ struct OpLift {
 template <int P>
 struct OpNorm {
     SpinorPtr a;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> A;
         Prec<P>::load(a, cb, A);
-        acc[0] += norm2_sp(A);
+        acc_norm2(acc[0], A);
     }
 };
 
@@ -287,13 +340,14 @@ struct OpNorm {
 template <int P>
 struct OpDot {
     SpinorPtr a, b;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> A, B;
         Prec<P>::load(a, cb, A);
         Prec<P>::load(b, cb, B);
-        dot_sp(A, B, acc[0], acc[1]);
+        acc_dot(A, B, acc[0], acc[1]);
     }
 };
 
@@ -301,14 +355,15 @@ struct OpDot {
 template <int P>
 struct OpOmega {
     SpinorPtr t, r;
-    __device__ void operator()(int cb, double *acc) const
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
     {
         using T = typename Prec<P>::T;
         Spinor<T> A, B;
         Prec<P>::load(t, cb, A);
         Prec<P>::load(r, cb, B);
-        dot_sp(A, B, acc[0], acc[1]);
-        acc[2] += norm2_sp(A);
+        acc_dot(A, B, acc[0], acc[1]);
+        acc_norm2(acc[2], A);
     }
 };
 

@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -37,6 +38,18 @@ namespace qcd {
 constexpr int SB = 32;  // sites per block of the site-blocked layout
 
 __host__ __device__ inline long pad_sites(long n) { return (n + SB - 1) / SB * SB; }
+
+// Programmatic dependent launch: the solver's kernels are launched so that
+// the next kernel's blocks may become resident while the previous kernel's
+// last wave and its grid reduction drain.  Every such kernel first waits
+// until its predecessor has completed and its writes are visible, then lets
+// its own successor launch.  Both are no-ops for a kernel launched without
+// the attribute.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 // Loads of data that one kernel reads exactly once (the links and the clover
 // blocks of a MULT: every link joins one site of each parity): no L1
@@ -217,6 +230,13 @@ __device__ __forceinline__ df fma(df a, df b, df c)
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
 __device__ __forceinline__ double to_d(df x) { return (double)x; }
+// a site's partial sum in arithmetic type T as a reduction value of type A
+template <class A>
+__device__ __forceinline__ A acc_cast(float x) { return A(x); }
+template <class A>
+__device__ __forceinline__ A acc_cast(double x) { return A(x); }
+template <class A>
+__device__ __forceinline__ A acc_cast(df x) { return A(to_d(x)); }
 
 template <class T>
 struct Spinor {

@@ -122,9 +122,13 @@ __device__ inline void finalize(int op, SolverState *st)
     }
 }
 
-// Reduce N doubles over the grid; blocks may be 1-D or 2-D.
-template <int N>
-__device__ __forceinline__ void grid_reduce(double v[N], const RedArgs &ra)
+// Reduce N values over the grid; blocks may be 1-D or 2-D.  The per-thread
+// values and the warp stage are in the accumulator type A (float for the
+// FP32 and FP16 levels, whose sums feed FP32 recurrences: GB300's FP64 rate
+// is 1/64 of its FP32 rate, and per-thread FP64 adds slowed those kernels
+// in proportion to their size); warp sums and everything after are FP64.
+template <int N, class A>
+__device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
 {
     __shared__ double sh[32][4];
     __shared__ int last;
@@ -137,19 +141,20 @@ __device__ __forceinline__ void grid_reduce(double v[N], const RedArgs &ra)
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < N; ++k) sh[wid][k] = v[k];
+        for (int k = 0; k < N; ++k) sh[wid][k] = (double)v[k];
     __syncthreads();
     if (wid == 0) {
+        double bsum[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) {
             double t = lane < nw ? sh[lane][k] : 0.0;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-            v[k] = t;
+            bsum[k] = t;
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < N; ++k) ra.partials[(size_t)blockIdx.x * 4 + k] = v[k];
+            for (int k = 0; k < N; ++k) ra.partials[(size_t)blockIdx.x * 4 + k] = bsum[k];
             __threadfence();
             unsigned t = atomicAdd(ra.counter, 1u);
             last = (t == gridDim.x - 1);

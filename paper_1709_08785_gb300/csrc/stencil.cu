@@ -21,6 +21,7 @@ template <int P, int MODE, int RED, bool DAG>
 __device__ __forceinline__ void stencil_body(const StencilArgs &A)
 {
     using T = typename Prec<P>::T;
+    pdl_enter();
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0;
     if (A.done && *A.done) {
         if (A.skip && lead) *A.skip = 1;
@@ -29,7 +30,9 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
     if (A.skip && lead) *A.skip = 0;
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = threadIdx.y;
-    double red[4] = {0.0, 0.0, 0.0, 0.0};
+    // reduction type: float at the FP32 / FP16 levels (see grid_reduce)
+    using RA = typename std::conditional<P == QCD_F32 || P == QCD_F16, float, double>::type;
+    RA red[4] = {RA(0), RA(0), RA(0), RA(0)};
     if (cb < A.g.Vh) {
         const SpinorPtr in = rhs_ptr(A.in, r, A.rhs_stride, A.norm_stride);
         const SpinorPtr out = rhs_ptr(A.out, r, A.rhs_stride, A.norm_stride);
@@ -59,9 +62,9 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
                         di += o.r * v.i - o.i * v.r;
                         nn += o.r * o.r + o.i * o.i;
                     }
-                red[0] = to_d(dr);
-                red[1] = to_d(di);
-                red[2] = to_d(nn);
+                red[0] = acc_cast<RA>(dr);
+                red[1] = acc_cast<RA>(di);
+                red[2] = acc_cast<RA>(nn);
             }
         } else if (MODE == M_SRC) {
             Spinor<T> y;
@@ -91,19 +94,19 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
                     dr += a.r * o.r + a.i * o.i;
                     di += a.r * o.i - a.i * o.r;
                 }
-            red[0] = to_d(dr);
-            red[1] = to_d(di);
+            red[0] = acc_cast<RA>(dr);
+            red[1] = acc_cast<RA>(di);
         } else if (RED == R_NORM) {
             T nn = 0;
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
                 for (int i = 0; i < 3; ++i) nn += acc.s[s][i].r * acc.s[s][i].r + acc.s[s][i].i * acc.s[s][i].i;
-            red[0] = to_d(nn);
+            red[0] = acc_cast<RA>(nn);
         }
         Prec<P>::store(out, cb, acc);
     }
-    if constexpr (RED != R_NONE) grid_reduce<3>(red, A.red);
+    if constexpr (RED != R_NONE) grid_reduce<RED == R_OMEGA ? 3 : RED == R_DOT_AUX ? 2 : 1>(red, A.red);
 }
 
 // Two register budgets of the same kernel; the autotuner picks one per
@@ -299,11 +302,11 @@ static void launch_t(const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s
 {
     if constexpr (P == QCD_F32 || P == QCD_F16) {
         if (variant == 1) {
-            stencil_kernel_r80<P, MODE, RED, DAG><<<grid, block, 0, s>>>(A);
+            launch_pdl(stencil_kernel_r80<P, MODE, RED, DAG>, grid, block, 0, s, A);
             return;
         }
     }
-    stencil_kernel<P, MODE, RED, DAG><<<grid, block, 0, s>>>(A);
+    launch_pdl(stencil_kernel<P, MODE, RED, DAG>, grid, block, 0, s, A);
 }
 
 template <int P>
@@ -415,8 +418,11 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
         set_error_message("reduction grid too large");
         return QCD_EINVAL;
     }
-    ProfScope prof(c, p == QCD_F32 ? QCD_K_MULT_F32 : p == QCD_F16 ? QCD_K_MULT_F16 : QCD_K_MULT_F64,
-                   stencil_bytes(c, sc));
+    const int cls = p == QCD_F32    ? (sc.mode == M_DHAT ? QCD_K_DHAT_F32 : QCD_K_MULT_F32)
+                    : p == QCD_F16  ? QCD_K_MULT_F16
+                    : p == QCD_DF64 ? QCD_K_MULT_DF64
+                                    : QCD_K_MULT_F64;
+    ProfScope prof(c, cls, stencil_bytes(c, sc));
     A.skip = prof.flag;
     int rc;
     if (p == QCD_F32 && nrhs > 1 && sc.red == R_NONE && (sc.mode == M_MULT || sc.mode == M_HOP))
