@@ -150,7 +150,7 @@ def oracle_sample(dims, U, b, W, reps):
 def oracle_iterations():
     p = os.path.join(ROOT, "oracle", "iteration_counts.json")
     if os.path.exists(p):
-        return json.load(open(p))["c2_fp64_eo"]["fp64_eo_bicgstab_iterations"]
+        return json.load(open(p))["fp64_eo_24x24x24x48"]["fp64_eo_bicgstab_iterations"]
     return None
 
 

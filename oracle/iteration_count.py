@@ -46,7 +46,7 @@ def main():
                seconds_single_core=secs, host=platform.machine(), cpu=platform.processor())
     path = os.path.join(HERE, "iteration_counts.json")
     with open(path, "w") as f:
-        json.dump({"c2_fp64_eo": out}, f, indent=1)
+        json.dump({"fp64_eo_24x24x24x48": out}, f, indent=1)
     print(json.dumps(out))
 
 

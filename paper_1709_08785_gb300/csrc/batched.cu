@@ -43,6 +43,7 @@ constexpr int S32_LEVEL = 0;
 struct BProb {
     Geom g;
     double k2;  // kappa^2
+    float k2f;  // kappa^2 rounded to FP32 on the host, for the FP32 phases
     GaugePtr U32, U64;
     CloverPtr Ci32, Ci64;
     SpinorPtr x, r, rt, p, q, t, tmp;          // FP32 inner (tmp: odd parity)
@@ -185,7 +186,7 @@ __device__ void run_phase(const BatchArgs &A, int ph)
                 apply_clover<C32>(pr.Ci32, 0, cb, a);
                 const SpinorPtr yv = ph == PH_DHAT_Q ? pr.p : pr.r;
                 Prec<C32>::load(yv, cb, y);
-                axpby_sp(a, float(-pr.k2), a, 1.0f, y);
+                axpby_sp(a, -pr.k2f, a, 1.0f, y);
                 Prec<C32>::store(ph == PH_DHAT_Q ? pr.q : pr.t, cb, a);
                 if (ph == PH_DHAT_Q) {
                     Spinor<float> w;
@@ -456,6 +457,7 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         BProb &pr = host[i];
         pr.g = c->g;
         pr.k2 = c->kappa * c->kappa;
+        pr.k2f = (float)pr.k2;
         for (int par = 0; par < 2; ++par) {
             pr.U32.a[par] = c->U32[par];
             pr.U32.b[par] = nullptr;

@@ -59,6 +59,8 @@ struct SolverState {
     int status;        // qcd_status
     int exit_half;     // 1: stopped after the first half-step of Alg. 2
     int pad[3];
+    float coef[6];     // alpha, omega, beta rounded to FP32 by the finaliser, for the
+                       // FP32 / FP16 levels (no per-site FP64 conversion)
 };
 
 // Finaliser run by the last block of a reduction kernel.

@@ -120,6 +120,11 @@ __device__ inline void finalize(int op, SolverState *st)
         else if (op >= FIN_ADDN && op < FIN_ADDN + 4) st->norm2[op - FIN_ADDN] += s[0];
         break;
     }
+    for (int k = 0; k < 2; ++k) {
+        st->coef[k] = (float)st->alpha[k];
+        st->coef[2 + k] = (float)st->omega[k];
+        st->coef[4 + k] = (float)st->beta[k];
+    }
 }
 
 // Reduce N values over the grid; blocks may be 1-D or 2-D.  The per-thread

@@ -44,11 +44,11 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
             clover_any<P>(A.C,A.out_par, cb, acc);
             Spinor<T> y;
             Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
-            axpby_sp(acc, T(A.cc), acc, T(A.a), y);
-            if (A.d != 0.0) {
+            axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
+            if (A.has_z) {
                 Spinor<T> z;
                 Prec<P>::load(rhs_ptr(A.z, r, A.rhs_stride, A.norm_stride), cb, z);
-                axpby_sp(acc, T(1), acc, T(A.d), z);
+                axpby_sp(acc, T(1), acc, sarg<T>(A.d, A.df32), z);
             }
             if (RED == R_OMEGA) {  // <out|aux>, |out|^2 (aux is usually y)
                 if (A.aux.p != A.y.p) Prec<P>::load(rhs_ptr(A.aux, r, A.rhs_stride, A.norm_stride), cb, y);
@@ -69,17 +69,17 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
         } else if (MODE == M_SRC) {
             Spinor<T> y;
             Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
-            axpby_sp(acc, T(A.cc), acc, T(A.a), y);
+            axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
             clover_any<P>(A.C,A.out_par, cb, acc);
         } else if (MODE == M_FULL) {
             Spinor<T> y;
             Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
             clover_any<P>(A.C,A.out_par, cb, y);
-            axpby_sp(acc, T(A.cc), acc, T(A.a), y);
-            if (A.d != 0.0) {
+            axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
+            if (A.has_z) {
                 Spinor<T> z;
                 Prec<P>::load(rhs_ptr(A.z, r, A.rhs_stride, A.norm_stride), cb, z);
-                axpby_sp(acc, T(1), acc, T(A.d), z);
+                axpby_sp(acc, T(1), acc, sarg<T>(A.d, A.df32), z);
             }
         }
         if (RED == R_DOT_AUX) {  // <aux|out>
@@ -121,6 +121,14 @@ __global__ void __launch_bounds__(384) stencil_kernel(StencilArgs A)
 
 template <int P, int MODE, int RED, bool DAG>
 __global__ void __maxnreg__(80) stencil_kernel_r80(StencilArgs A)
+{
+    stencil_body<P, MODE, RED, DAG>(A);
+}
+
+// DF64 (arithmetic-bound, ~165 registers by default): a 128-register cap
+// gives four 128-thread blocks per SM instead of three
+template <int P, int MODE, int RED, bool DAG>
+__global__ void __maxnreg__(128) stencil_kernel_r128(StencilArgs A)
 {
     stencil_body<P, MODE, RED, DAG>(A);
 }
@@ -306,6 +314,12 @@ static void launch_t(const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s
             return;
         }
     }
+    if constexpr (P == QCD_DF64) {
+        if (variant == 1) {
+            launch_pdl(stencil_kernel_r128<P, MODE, RED, DAG>, grid, block, 0, s, A);
+            return;
+        }
+    }
     launch_pdl(stencil_kernel<P, MODE, RED, DAG>, grid, block, 0, s, A);
 }
 
@@ -391,6 +405,10 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
     A.a = sc.a;
     A.cc = sc.cc;
     A.d = sc.d;
+    A.af = (float)sc.a;
+    A.ccf = (float)sc.cc;
+    A.df32 = (float)sc.d;
+    A.has_z = sc.d != 0.0;
     A.rhs_stride = sc.rhs_stride;
     A.norm_stride = sc.norm_stride;
     A.red = sc.red_args;

@@ -295,12 +295,23 @@ struct StencilArgs {
     SpinorPtr out, in, y, aux, z;
     int out_par;
     double a, cc, d;
+    float af, ccf, df32;  // the same rounded on the host, for the FP32 / FP16 kernels
+    int has_z;            // d != 0
     size_t rhs_stride;   // in 16-byte elements
     size_t norm_stride;  // in floats
     RedArgs red;
     const int *done;
     int *skip;  // profiling: set to 1 when the launch returns early
 };
+
+// a host-supplied scalar in the kernel's arithmetic type (float: the
+// host-rounded copy, so no FP64 conversion runs per thread)
+template <class T>
+__device__ __forceinline__ T sarg(double d, float f)
+{
+    if constexpr (std::is_same<T, float>::value) return f;
+    else return T(d);
+}
 
 __device__ __forceinline__ SpinorPtr rhs_ptr(const SpinorPtr &v, int r, size_t stride, size_t nstride)
 {

@@ -1,7 +1,8 @@
 // Autotuner for the stencil kernels: for each launch configuration the
 // solvers use (precision, mode, fused reduction, dagger, right-hand sides) it
-// times every candidate -- register budget (compiler's / capped at 80) x
-// threads per block along the sites -- on scratch buffers with L2 evicted
+// times every candidate -- register budget (compiler's / capped at 80 for FP32
+// and FP16, at 128 for DF64) x threads per block along the sites -- on
+// scratch buffers with L2 evicted
 // before each launch, keeps the fastest, and stores the choice in a JSON
 // cache keyed by device name, lattice and configuration.  Launches that have
 // no tuned entry use the default (compiler's budget, 128 sites per block).
@@ -138,7 +139,7 @@ int tune_one(qcd_ctx *c, StencilCall s, qcd_ctx::TuneEntry *out)
     s.norm_stride = (size_t)c->g.Vh_pad;
     s.red_args = RedArgs{c->partials, c->counters, c->states + ST_TUNE, FIN_NONE};
     s.done = nullptr;
-    const int nv = (s.prec == QCD_F32 || s.prec == QCD_F16) ? 2 : 1;
+    const int nv = (s.prec == QCD_F32 || s.prec == QCD_F16 || s.prec == QCD_DF64) ? 2 : 1;
     const int bxs1[] = {64, 128, 256}, bxsn[] = {32, 64};
     const int *bxs = s.nrhs > 1 ? bxsn : bxs1;
     const int nbx = s.nrhs > 1 ? 2 : 3;

@@ -39,7 +39,7 @@ def rel(a, b):
 
 
 @pytest.fixture(scope="module")
-def c2():
+def lat24():
     from paper_1709_08785_gb300 import qcd
 
     dims, kappa, csw, t_bc = (24, 24, 24, 48), 0.124, 1.6, -1
@@ -54,45 +54,45 @@ def c2():
 
 
 @pytest.mark.parametrize("prec", [0, 3, 1, 2])
-def test_c2_mult_sampled(c2, prec):
-    dims = c2["dims"]
+def test_24c48_mult_sampled(lat24, prec):
+    dims = lat24["dims"]
     Vh = inputs.volume(dims) // 2
     v = inputs.gaussian_source(dims, 70)[:Vh]
     dt = torch.complex128 if prec in (0, 3) else torch.complex64
     inp = torch.from_numpy(v).to(dt).cuda()
     out = torch.zeros_like(inp)
-    c2["ctx"].mult_eo(out, inp, 0, False, prec)
+    lat24["ctx"].mult_eo(out, inp, 0, False, prec)
     torch.cuda.synchronize()
     cbs = np.random.default_rng(71).choice(Vh, 96, replace=False)
-    want = mult_sampled(dims, c2["t_bc"], c2["U"], c2["kappa"], c2["csw"], v, 0, cbs)
+    want = mult_sampled(dims, lat24["t_bc"], lat24["U"], lat24["kappa"], lat24["csw"], v, 0, cbs)
     got = out.cpu().numpy().astype(np.complex128)[cbs]
     assert rel(got, want) < TOL[prec]
 
 
-def test_c2_dirac_sampled(c2):
-    dims = c2["dims"]
+def test_24c48_dirac_sampled(lat24):
+    dims = lat24["dims"]
     v = inputs.gaussian_source(dims, 72)
     inp = torch.from_numpy(v).cuda()
     out = torch.zeros_like(inp)
-    c2["ctx"].dirac(out, inp)
+    lat24["ctx"].dirac(out, inp)
     torch.cuda.synchronize()
     sites = np.random.default_rng(73).choice(inputs.volume(dims), 96, replace=False)
-    want = oracle.dirac_sites(dims, c2["t_bc"], c2["U"], c2["kappa"], c2["csw"], v, sites)
+    want = oracle.dirac_sites(dims, lat24["t_bc"], lat24["U"], lat24["kappa"], lat24["csw"], v, sites)
     assert rel(out.cpu().numpy()[sites], want) < 1e-13
 
 
-def test_c2_mixed_solve_true_residual(c2):
-    bd = torch.from_numpy(c2["b"]).cuda()
+def test_24c48_mixed_solve_true_residual(lat24):
+    bd = torch.from_numpy(lat24["b"]).cuda()
     x = torch.zeros_like(bd)
-    info = c2["ctx"].solve(bd, x, tol=1e-12, precision_levels=2)
+    info = lat24["ctx"].solve(bd, x, tol=1e-12, precision_levels=2)
     assert info["status"] == 0 and info["true_resid"] <= 1e-12
-    F = oracle.clover_field(c2["dims"], c2["U"], c2["kappa"], c2["csw"])
-    r = oracle.true_residual(c2["dims"], c2["t_bc"], c2["U"], F, c2["kappa"], c2["b"], x.cpu().numpy())
+    F = oracle.clover_field(lat24["dims"], lat24["U"], lat24["kappa"], lat24["csw"])
+    r = oracle.true_residual(lat24["dims"], lat24["t_bc"], lat24["U"], F, lat24["kappa"], lat24["b"], x.cpu().numpy())
     assert r <= 1e-12, r
 
 
 @pytest.fixture(scope="module")
-def c3():
+def lat48():
     from paper_1709_08785_gb300 import qcd
 
     dims, kappa, csw, t_bc = (48, 48, 48, 96), 0.124, 1.6, -1
@@ -109,28 +109,28 @@ def c3():
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-def test_c3_mult_sampled(c3, prec):
-    dims = c3["dims"]
+def test_48c96_mult_sampled(lat48, prec):
+    dims = lat48["dims"]
     Vh = inputs.volume(dims) // 2
     v = inputs.gaussian_source(dims, 74)[:Vh]
     inp = torch.from_numpy(v).to(torch.complex64).cuda()
     out = torch.zeros_like(inp)
-    c3["ctx"].mult_eo(out, inp, 1, False, prec)
+    lat48["ctx"].mult_eo(out, inp, 1, False, prec)
     torch.cuda.synchronize()
     cbs = np.random.default_rng(75).choice(Vh, 96, replace=False)
-    want = mult_sampled(dims, c3["t_bc"], c3["U"], c3["kappa"], c3["csw"], v, 1, cbs)
+    want = mult_sampled(dims, lat48["t_bc"], lat48["U"], lat48["kappa"], lat48["csw"], v, 1, cbs)
     got = out.cpu().numpy().astype(np.complex128)[cbs]
     assert rel(got, want) < TOL[prec]
 
 
-def test_c3_three_level_solve_sampled_residual(c3):
-    bd = torch.from_numpy(c3["b"]).cuda()
+def test_48c96_three_level_solve_sampled_residual(lat48):
+    bd = torch.from_numpy(lat48["b"]).cuda()
     x = torch.zeros_like(bd)
-    info = c3["ctx"].solve(bd, x, tol=1e-12, precision_levels=3, inner_tol=[1e-5, 1e-2])
+    info = lat48["ctx"].solve(bd, x, tol=1e-12, precision_levels=3, inner_tol=[1e-5, 1e-2])
     assert info["status"] == 0 and info["true_resid"] <= 1e-12, info
     assert info["dhat_applies"][2] > 0
-    sites = np.random.default_rng(76).choice(inputs.volume(c3["dims"]), 512, replace=False)
+    sites = np.random.default_rng(76).choice(inputs.volume(lat48["dims"]), 512, replace=False)
     xs = x.cpu().numpy()
-    Dx = oracle.dirac_sites(c3["dims"], c3["t_bc"], c3["U"], c3["kappa"], c3["csw"], xs, sites)
-    r = np.linalg.norm((c3["b"][sites] - Dx).ravel()) / np.linalg.norm(c3["b"][sites].ravel())
+    Dx = oracle.dirac_sites(lat48["dims"], lat48["t_bc"], lat48["U"], lat48["kappa"], lat48["csw"], xs, sites)
+    r = np.linalg.norm((lat48["b"][sites] - Dx).ravel()) / np.linalg.norm(lat48["b"][sites].ravel())
     assert r <= 1e-12, r

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def c1():
+def lat4():
     """4^4, links exp(i 0.3 H) seed 1, kappa 0.12, csw 1.0, antiperiodic in
     time, Gaussian source seed 2."""
     from paper_1709_08785_gb300 import qcd
@@ -35,7 +35,7 @@ def c1():
 
 
 @pytest.fixture(scope="module")
-def c2s():
+def lat8():
     """A reduced copy of the 24^3x48 workload's parameters (eps 0.25,
     kappa 0.124, csw 1.6) on 8^3x16, for the nested and three-level solves."""
     from paper_1709_08785_gb300 import qcd
@@ -63,27 +63,27 @@ def true_res(P, x):
     return oracle.true_residual(P["dims"], P["t_bc"], P["U"], P["F"], P["kappa"], P["b"], x)
 
 
-def test_unpreconditioned_fp64(c1):
-    x, info = solve(c1, precision_levels=1, even_odd=0)
+def test_unpreconditioned_fp64(lat4):
+    x, info = solve(lat4, precision_levels=1, even_odd=0)
     assert info["status"] == 0
-    assert true_res(c1, x) <= 1e-12
-    assert abs(info["true_resid"] - true_res(c1, x)) <= 1e-13
-    assert np.linalg.norm(x - c1["xo"]) / np.linalg.norm(c1["xo"]) < 1e-10
+    assert true_res(lat4, x) <= 1e-12
+    assert abs(info["true_resid"] - true_res(lat4, x)) <= 1e-13
+    assert np.linalg.norm(x - lat4["xo"]) / np.linalg.norm(lat4["xo"]) < 1e-10
 
 
 @pytest.mark.parametrize("levels", [1, 2, 3])
-def test_even_odd_solves_c1(c1, levels):
-    x, info = solve(c1, precision_levels=levels)
+def test_even_odd_solves_4c4(lat4, levels):
+    x, info = solve(lat4, precision_levels=levels)
     assert info["status"] == 0, info
-    assert true_res(c1, x) <= 1e-12
-    assert np.linalg.norm(x - c1["xo"]) / np.linalg.norm(c1["xo"]) < 1e-10
+    assert true_res(lat4, x) <= 1e-12
+    assert np.linalg.norm(x - lat4["xo"]) / np.linalg.norm(lat4["xo"]) < 1e-10
 
 
 @pytest.mark.parametrize("levels", [1, 2, 3])
-def test_even_odd_solves_8c16(c2s, levels):
-    x, info = solve(c2s, precision_levels=levels)
+def test_even_odd_solves_8c16(lat8, levels):
+    x, info = solve(lat8, precision_levels=levels)
     assert info["status"] == 0, info
-    r = true_res(c2s, x)
+    r = true_res(lat8, x)
     assert r <= 1e-12, (r, info)
     if levels >= 2:
         assert info["dhat_applies"][1] > 0 and info["outer_iters"] >= 1
@@ -92,49 +92,49 @@ def test_even_odd_solves_8c16(c2s, levels):
 
 
 @pytest.mark.parametrize("levels", [2, 3])
-def test_fp64_outer_arithmetic(c2s, levels):
+def test_fp64_outer_arithmetic(lat8, levels):
     """The nested schemes with the outer level in FP64 instead of DF64."""
-    x, info = solve(c2s, precision_levels=levels, outer_df64=0)
+    x, info = solve(lat8, precision_levels=levels, outer_df64=0)
     assert info["status"] == 0, info
-    assert true_res(c2s, x) <= 1e-12
+    assert true_res(lat8, x) <= 1e-12
 
 
-def test_host_buffers(c1):
-    x = np.zeros_like(c1["b"])
-    info = c1["ctx"].solve(c1["b"], x, tol=1e-12, precision_levels=2)
+def test_host_buffers(lat4):
+    x = np.zeros_like(lat4["b"])
+    info = lat4["ctx"].solve(lat4["b"], x, tol=1e-12, precision_levels=2)
     assert info["status"] == 0
-    assert true_res(c1, x) <= 1e-12
+    assert true_res(lat4, x) <= 1e-12
 
 
-def test_warm_start_from_solution(c1):
-    bd = torch.from_numpy(c1["b"]).cuda()
-    x = torch.from_numpy(c1["xo"]).cuda()
-    info = c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, use_x0=1)
+def test_warm_start_from_solution(lat4):
+    bd = torch.from_numpy(lat4["b"]).cuda()
+    x = torch.from_numpy(lat4["xo"]).cuda()
+    info = lat4["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, use_x0=1)
     assert info["status"] == 0 and info["outer_iters"] <= 1
-    assert true_res(c1, x.cpu().numpy()) <= 1e-12
+    assert true_res(lat4, x.cpu().numpy()) <= 1e-12
 
 
-def test_zero_source(c1):
-    bd = torch.zeros_like(torch.from_numpy(c1["b"])).cuda()
+def test_zero_source(lat4):
+    bd = torch.zeros_like(torch.from_numpy(lat4["b"])).cuda()
     x = torch.ones_like(bd)
-    info = c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, check=False)
+    info = lat4["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, check=False)
     assert info["rc"] == 0
     assert torch.count_nonzero(x).item() == 0
 
 
-def test_nonfinite_source(c1):
-    b = c1["b"].copy()
+def test_nonfinite_source(lat4):
+    b = lat4["b"].copy()
     b[3, 1, 2] = np.nan
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bd)
-    info = c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, check=False)
+    info = lat4["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, check=False)
     assert info["rc"] == -6  # QCD_ENONFINITE
 
 
-def test_singular_clover_block_reported(c1):
+def test_singular_clover_block_reported(lat4):
     """A clover block whose LDL^H pivots are not finite (one NaN link) is
     reported as QCD_ECLOVER_SINGULAR; a good field afterwards builds again."""
-    qcd = c1["qcd"]
+    qcd = lat4["qcd"]
     dims = (4, 4, 4, 4)
     U = inputs.random_gauge(dims, 0.3, 1)
     bad = U.copy()
@@ -149,22 +149,22 @@ def test_singular_clover_block_reported(c1):
     ctx.close()
 
 
-def test_iteration_cap(c1):
-    bd = torch.from_numpy(c1["b"]).cuda()
+def test_iteration_cap(lat4):
+    bd = torch.from_numpy(lat4["b"]).cuda()
     x = torch.zeros_like(bd)
-    info = c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=1, max_outer=1, max_restarts=0, check=False)
+    info = lat4["ctx"].solve(bd, x, tol=1e-12, precision_levels=1, max_outer=1, max_restarts=0, check=False)
     assert info["rc"] == -4  # QCD_ENOTCONV
     assert info["true_resid"] > 1e-12
 
 
-def test_invalid_arguments(c1):
-    qcd = c1["qcd"]
-    bd = torch.from_numpy(c1["b"]).cuda()
+def test_invalid_arguments(lat4):
+    qcd = lat4["qcd"]
+    bd = torch.from_numpy(lat4["b"]).cuda()
     x = torch.zeros_like(bd)
     with pytest.raises(qcd.QCDError):
-        c1["ctx"].solve(bd, x, tol=-1.0)
+        lat4["ctx"].solve(bd, x, tol=-1.0)
     with pytest.raises(qcd.QCDError):
-        c1["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, even_odd=0)
+        lat4["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, even_odd=0)
     with pytest.raises(qcd.QCDError):
         qcd.Context((4, 4, 3, 4))
     ctx = qcd.Context((4, 4, 4, 4))
@@ -175,8 +175,8 @@ def test_invalid_arguments(c1):
     ctx.close()
 
 
-def test_solve_repeatable_bitwise(c2s):
-    x1, i1 = solve(c2s, precision_levels=2)
-    x2, i2 = solve(c2s, precision_levels=2)
+def test_solve_repeatable_bitwise(lat8):
+    x1, i1 = solve(lat8, precision_levels=2)
+    x2, i2 = solve(lat8, precision_levels=2)
     assert np.array_equal(x1, x2)
     assert i1["inner_iters"] == i2["inner_iters"]
