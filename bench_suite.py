@@ -113,15 +113,25 @@ def w_point_sources(args):
     # batch would need one context, i.e. one copy of the fields, per source)
     del U
     P = inputs.point_sources(dims)
+    X = torch.zeros((12,) + P.shape[1:], dtype=torch.complex128, device="cuda")
     seq, res, outer = 0.0, [], []
     for k in range(12):
         bk = torch.from_numpy(np.ascontiguousarray(P[k])).cuda()
-        xk = torch.zeros_like(bk)
-        t1, info = timed_solve(torch, ctx, bk, xk, tol, reps=1, precision_levels=2)
+        t1, info = timed_solve(torch, ctx, bk, X[k], tol, reps=1, precision_levels=2)
         seq += t1
         res.append(info["true_resid"])
         outer.append(info["outer_iters"])
     out["solves"] = {"sequential_s": round(seq, 4), "max_true_resid": max(res), "outer_iters": outer}
+    # the pion two-point function of the 12-column propagator
+    ctx.pion_correlator(X, 12)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    C = ctx.pion_correlator(X, 12)
+    dt = time.perf_counter() - t
+    Lt = dims[3]
+    meff = [float(np.log(C[k] / C[k + 1])) for k in range(1, Lt // 2)]
+    out["pion_correlator"] = {"ms": round(dt * 1e3, 3), "C_t": [float(c) for c in C[: Lt // 2 + 1]],
+                              "effective_mass_t1_to_half": [round(m, 4) for m in meff]}
     return out
 
 

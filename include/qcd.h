@@ -311,6 +311,20 @@ int qcd_mult_benchmark(qcd_ctx *ctx, int prec, int nrhs, int iters, double *ms_p
 int qcd_mult_throughput(qcd_ctx *ctx, int prec, int nrhs, int iters, double *ms_per_launch,
                         double *bytes_per_launch);
 
+/* Pion two-point function from propagator columns (Sec. II-A: the solutions
+ * of Eq. 1 feed expectation values of observables made of quarks).  S holds
+ * ncol full-lattice solutions one after another, each complex128 in the
+ * canonical layout of qcd_solve's x ([V][spin 4][colour 3], V in the order
+ * [t][z][y][x]), on the device (on_device != 0) or in host memory.  With S the
+ * 12 spin-colour columns of the propagator from a point source,
+ * gamma5-hermiticity makes the pion correlator
+ *     C(t) = sum_columns sum_{x in timeslice t} sum_{spin,colour} |S(x)|^2,
+ * which is written to the host array C[Lt] (caller-owned).  Sums run in
+ * FP64 in a fixed order (bitwise repeatable).  Synchronous.  QCD_EINVAL for a
+ * NULL pointer or ncol < 1; host columns are staged one at a time through a
+ * device buffer of one column. */
+int qcd_pion_correlator(qcd_ctx *ctx, const void *S, int ncol, int on_device, double *C);
+
 const char *qcd_strerror(int status);
 const char *qcd_last_error(void);
 

@@ -157,6 +157,21 @@ def site_of_cb(dims, parity, cb):
     return np.where((x + y + z + t) % 2 == parity, s, s + 1)
 
 
+# ---------------------------------------------------------------- observables
+def pion_correlator(dims, S):
+    """C(t) = sum over columns, over the sites x of timeslice t and over spin
+    and colour of |S(x)|^2, for propagator columns S [ncol, V, 4, 3] (sites
+    lexicographic, t slowest).  With S the 12 spin-colour columns from a point
+    source this is the pion two-point function sum_x Tr[S(x) S(x)^dag]
+    (gamma5-hermiticity, Eq. 3 with g5 D g5 = D^dag), an observable the
+    solutions of Eq. 1 serve (Sec. II-A)."""
+    S = np.asarray(S)
+    Lt = int(dims[3])
+    V3 = volume(dims) // Lt
+    a = np.abs(S.reshape(S.shape[0], Lt, V3, 12)) ** 2
+    return a.sum(axis=(0, 2, 3))
+
+
 # ---------------------------------------------------------------- even-odd
 def half_to_full(dims, parity, half):
     half = _c(half)

@@ -818,6 +818,15 @@ extern "C" int qcd_mult_throughput(qcd_ctx *c, int prec, int nrhs, int iters, do
     return QCD_OK;
 }
 
+extern "C" int qcd_pion_correlator(qcd_ctx *c, const void *S, int ncol, int on_device, double *C)
+{
+    if (!c || !S || !C || ncol < 1) {
+        set_error_message("qcd_pion_correlator: NULL pointer or ncol < 1");
+        return QCD_EINVAL;
+    }
+    return pion_correlator(c, S, ncol, on_device, C);
+}
+
 extern "C" const char *qcd_strerror(int s)
 {
     switch (s) {

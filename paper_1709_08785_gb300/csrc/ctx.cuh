@@ -230,6 +230,8 @@ int tune_entries(qcd_ctx *c, int max, unsigned *keys, int *variant, int *bx, dou
 
 // force.cu
 int force(qcd_ctx *c, const void *x, const void *lam, void *G, const void *U_canon);
+// correlator.cu
+int pion_correlator(qcd_ctx *c, const void *S, int ncol, int on_device, double *C_host);
 int gamma5_full(qcd_ctx *c, const void *in, void *out);
 
 }  // namespace qcd

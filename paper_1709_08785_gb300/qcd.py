@@ -68,7 +68,7 @@ EXPORTS = [
     "qcd_set_profiling", "qcd_kernel_stats", "qcd_reset_kernel_stats", "qcd_strerror", "qcd_last_error",
     "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_mult_throughput", "qcd_dslash_eo_noalloc",
     "qcd_solve_adjoint", "qcd_force", "qcd_autotune", "qcd_tune_info", "qcd_solve_batched", "qcd_set_wait_limit",
-    "qcd_set_graphs",
+    "qcd_set_graphs", "qcd_pion_correlator",
 ]
 
 _lib = None
@@ -125,6 +125,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
                                       ctypes.POINTER(dp), ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
     lib.qcd_set_wait_limit.argtypes = [ctypes.c_longlong]
     lib.qcd_set_graphs.argtypes = [ip]
+    lib.qcd_pion_correlator.argtypes = [vp, vp, ip, ip, ctypes.POINTER(dp)]
     lib.qcd_autotune.argtypes = [vp, ctypes.c_char_p]
     lib.qcd_tune_info.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ip), ctypes.POINTER(ip),
                                   ctypes.POINTER(dp)]
@@ -324,6 +325,18 @@ class Context:
         _check(self.lib.qcd_mult_benchmark(self._h, int(prec), int(nrhs), int(iters), ctypes.byref(ms),
                                            ctypes.byref(by)))
         return dict(ms=ms.value, bytes=by.value, gbs=by.value / (ms.value * 1e-3) / 1e9)
+
+    def pion_correlator(self, S, ncol: int = 12):
+        """C(t) of qcd_pion_correlator from ncol propagator columns stored one
+        after another in S (a torch CUDA tensor, or host memory)."""
+        import numpy as np
+
+        Lt = self.dims[3]
+        C = np.zeros(Lt, dtype=np.float64)
+        on_device = bool(getattr(S, "is_cuda", False))
+        _check(self.lib.qcd_pion_correlator(self._h, _ptr(S), int(ncol), int(on_device),
+                                            C.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return C
 
     def mult_throughput(self, prec: int = F32, nrhs: int = 1, iters: int = 100) -> dict:
         """Back-to-back MULT launches without cache eviction (qcd.h)."""

@@ -351,6 +351,56 @@ def test_sampled_site_helpers_match_the_full_lattice():
         assert np.array_equal(psi[oracle.site_of_cb(dims, par, cbs)], half)
 
 
+# ------------------------------------------------------------- pion correlator
+def test_pion_correlator_brute_force():
+    dims = (2, 2, 2, 4)
+    V = inputs.volume(dims)
+    rng = np.random.default_rng(31)
+    S = rng.standard_normal((3, V, 4, 3)) + 1j * rng.standard_normal((3, V, 4, 3))
+    want = np.zeros(dims[3])
+    for col in range(3):
+        for site in range(V):
+            t = site // (dims[0] * dims[1] * dims[2])
+            for sp in range(4):
+                for c in range(3):
+                    want[t] += abs(S[col, site, sp, c]) ** 2
+    assert rel(oracle.pion_correlator(dims, S), want) < 1e-14
+
+
+def test_pion_correlator_free_field_closed_form():
+    """Unit links, antiperiodic time: the oracle's 12 point-source solutions
+    give the pion correlator of the free propagator, which follows from the
+    closed-form D(p) = (1 - 2k sum cos p) + 2ik sum g_mu sin p_mu: S(x) is
+    the inverse Fourier transform of D(p)^-1 (x) 1_colour, so
+    C(t) = 3 sum_xvec ||S_spin(xvec, t)||^2 with S_spin from an FFT over the
+    momentum grid (p_t = pi (2n + 1) / Lt; the half-step shift is a phase)."""
+    dims, kappa, t_bc = (2, 4, 4, 6), 0.12, -1
+    U = inputs.unit_gauge(dims)
+    F = oracle.clover_field(dims, U, kappa, 1.3)
+    # dense D from the oracle's operator (BiCGStab from r~ = r0 = a point
+    # source breaks down exactly on the free field: rho vanishes by symmetry)
+    N = inputs.volume(dims) * 12
+    Dm = np.empty((N, N), dtype=complex)
+    e = np.zeros(N, dtype=complex)
+    for k in range(N):
+        e[k] = 1.0
+        Dm[:, k] = oracle.dirac(dims, t_bc, U, F, kappa, e.reshape(-1, 4, 3)).ravel()
+        e[k] = 0.0
+    B = inputs.point_sources(dims).reshape(12, N).T
+    cols = np.linalg.solve(Dm, B).T.reshape(12, -1, 4, 3)
+    got = oracle.pion_correlator(dims, cols)
+    n = [np.arange(L) for L in dims]
+    px, py, pz, pt = np.meshgrid(*[2 * np.pi * k / L for k, L in zip(n, dims)], indexing="ij")
+    pt = pt + np.pi / dims[3]
+    p = [px, py, pz, pt]
+    Dp = (1 - 2 * kappa * sum(np.cos(q) for q in p))[..., None, None] * np.eye(4)
+    Dp = Dp + 2j * kappa * sum(np.sin(p[mu])[..., None, None] * G[mu] for mu in range(4))
+    Ssp = np.fft.ifftn(np.linalg.inv(Dp), axes=(0, 1, 2, 3))  # [x, y, z, t, 4, 4]
+    want = 3 * (np.abs(Ssp) ** 2).sum(axis=(0, 1, 2, 4, 5))
+    assert rel(got, want) < 1e-12
+    assert np.allclose(want[1:], want[1:][::-1], rtol=1e-12)  # time reflection of the free correlator
+
+
 # ------------------------------------------------------------- P12 gradient
 def test_link_gradient_finite_differences():
     """dF/dh along U_l -> exp(i h T) U_l, by central differences of the
