@@ -208,6 +208,8 @@ struct StencilCall {
 };
 int launch_stencil(qcd_ctx *c, const StencilCall &s);
 unsigned tune_key(const StencilCall &s);
+// F32 hopping / MULT on several right-hand sides: the shared-memory staged kernel
+bool is_mrhs(const StencilCall &s);
 double stencil_bytes(const qcd_ctx *c, const StencilCall &s);  // algorithmic bytes of one launch
 int fill_pattern(qcd_ctx *c, int prec, HVec v, int nrhs, size_t rhs_stride, int seed);
 

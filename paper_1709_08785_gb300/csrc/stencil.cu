@@ -28,12 +28,15 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
         return;
     }
     if (A.skip && lead) *A.skip = 0;
-    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = threadIdx.y;
     // reduction type: float at the FP32 / FP16 levels (see grid_reduce)
     using RA = typename std::conditional<P == QCD_F32 || P == QCD_F16, float, double>::type;
     RA red[4] = {RA(0), RA(0), RA(0), RA(0)};
-    if (cb < A.g.Vh) {
+    // A.spt sites per thread, in block-sized steps so that each step's loads
+    // stay coalesced
+    for (int k = 0; k < A.spt; ++k) {
+        const int cb = (blockIdx.x * A.spt + k) * blockDim.x + threadIdx.x;
+        if (cb >= A.g.Vh) break;
         const SpinorPtr in = rhs_ptr(A.in, r, A.rhs_stride, A.norm_stride);
         const SpinorPtr out = rhs_ptr(A.out, r, A.rhs_stride, A.norm_stride);
         Spinor<T> acc;
@@ -62,9 +65,9 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
                         di += o.r * v.i - o.i * v.r;
                         nn += o.r * o.r + o.i * o.i;
                     }
-                red[0] = acc_cast<RA>(dr);
-                red[1] = acc_cast<RA>(di);
-                red[2] = acc_cast<RA>(nn);
+                red[0] += acc_cast<RA>(dr);
+                red[1] += acc_cast<RA>(di);
+                red[2] += acc_cast<RA>(nn);
             }
         } else if (MODE == M_SRC) {
             Spinor<T> y;
@@ -94,15 +97,15 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
                     dr += a.r * o.r + a.i * o.i;
                     di += a.r * o.i - a.i * o.r;
                 }
-            red[0] = acc_cast<RA>(dr);
-            red[1] = acc_cast<RA>(di);
+            red[0] += acc_cast<RA>(dr);
+            red[1] += acc_cast<RA>(di);
         } else if (RED == R_NORM) {
             T nn = 0;
 #pragma unroll
             for (int s = 0; s < 4; ++s)
 #pragma unroll
                 for (int i = 0; i < 3; ++i) nn += acc.s[s][i].r * acc.s[s][i].r + acc.s[s][i].i * acc.s[s][i].i;
-            red[0] = acc_cast<RA>(nn);
+            red[0] += acc_cast<RA>(nn);
         }
         Prec<P>::store(out, cb, acc);
     }
@@ -217,8 +220,8 @@ __device__ __forceinline__ void mrhs_body(const StencilArgs &A)
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x, cb = cb0 + lane, r = threadIdx.y;
-    if (cb >= A.g.Vh) return;
+    const int lane = threadIdx.x, cb = cb0 + lane, r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (cb >= A.g.Vh || r >= A.nrhs) return;
     const SpinorPtr in = rhs_ptr(A.in, r, A.rhs_stride, A.norm_stride);
     const SpinorPtr out = rhs_ptr(A.out, r, A.rhs_stride, A.norm_stride);
     const int tflag = s_tf[lane];
@@ -284,9 +287,12 @@ __global__ void __maxnreg__(80) mrhs_kernel_r80(StencilArgs A)
     mrhs_body<MODE, DAG>(A);
 }
 
-static int launch_mrhs(const StencilCall &sc, const StencilArgs &A, int nrhs, cudaStream_t s, int variant)
+// tile: right-hand sides per block (the links and clover of a 32-site block
+// are staged once per tile; the autotuner picks the tile)
+static int launch_mrhs(const StencilCall &sc, const StencilArgs &A, int nrhs, cudaStream_t s, int variant, int tile)
 {
-    dim3 block(SB, nrhs), grid(nblocks(A.g.Vh, SB));
+    if (tile < 1 || tile > nrhs) tile = nrhs;
+    dim3 block(SB, tile), grid(nblocks(A.g.Vh, SB), (nrhs + tile - 1) / tile);
     const size_t smem = MR_BYTES;
 #define QCD_MR(MODE, DAG)                                                                              \
     do {                                                                                               \
@@ -386,6 +392,11 @@ double stencil_bytes(const qcd_ctx *c, const StencilCall &sc)
     return per_site * c->g.Vh;
 }
 
+bool is_mrhs(const StencilCall &sc)
+{
+    return sc.prec == QCD_F32 && sc.nrhs > 1 && sc.red == R_NONE && (sc.mode == M_MULT || sc.mode == M_HOP);
+}
+
 int launch_stencil(qcd_ctx *c, const StencilCall &sc)
 {
     StencilArgs A;
@@ -411,6 +422,7 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
     A.has_z = sc.d != 0.0;
     A.rhs_stride = sc.rhs_stride;
     A.norm_stride = sc.norm_stride;
+    A.nrhs = sc.nrhs < 1 ? 1 : sc.nrhs;
     A.red = sc.red_args;
     A.done = sc.done;
     const int nrhs = sc.nrhs < 1 ? 1 : sc.nrhs;
@@ -418,8 +430,8 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
         set_error_message("nrhs > 16 per launch");
         return QCD_EINVAL;
     }
-    int bx = 128, variant = 0;
-    if (nrhs > 1) bx = nrhs <= 4 ? 64 : 32;
+    int bx = 128, variant = 0;  // bx: sites per block, or for the multi-RHS kernel the RHS tile
+    if (nrhs > 1) bx = is_mrhs(sc) ? nrhs : nrhs <= 4 ? 64 : 32;
     if (sc.force_variant >= 0) {
         variant = sc.force_variant;
         bx = sc.force_bx;
@@ -430,9 +442,11 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
             bx = it->second.bx;
         }
     }
+    // variant bit 0: register budget; bit 1: two sites per thread
+    A.spt = is_mrhs(sc) ? 1 : 1 + ((variant >> 1) & 1);
     dim3 block(bx, nrhs);
-    dim3 grid(nblocks(c->g.Vh, bx));
-    if (sc.red != R_NONE && (int)grid.x > c->partial_blocks) {
+    dim3 grid(nblocks(c->g.Vh, bx * A.spt));
+    if (!is_mrhs(sc) && sc.red != R_NONE && (int)grid.x > c->partial_blocks) {
         set_error_message("reduction grid too large");
         return QCD_EINVAL;
     }
@@ -443,12 +457,12 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
     ProfScope prof(c, cls, stencil_bytes(c, sc));
     A.skip = prof.flag;
     int rc;
-    if (p == QCD_F32 && nrhs > 1 && sc.red == R_NONE && (sc.mode == M_MULT || sc.mode == M_HOP))
-        rc = launch_mrhs(sc, A, nrhs, c->stream, variant);
-    else if (p == QCD_F64) rc = dispatch<QCD_F64>(sc, A, grid, block, c->stream, variant);
-    else if (p == QCD_F32) rc = dispatch<QCD_F32>(sc, A, grid, block, c->stream, variant);
-    else if (p == QCD_DF64) rc = dispatch<QCD_DF64>(sc, A, grid, block, c->stream, variant);
-    else rc = dispatch<QCD_F16>(sc, A, grid, block, c->stream, variant);
+    const int rv = variant & 1;
+    if (is_mrhs(sc)) rc = launch_mrhs(sc, A, nrhs, c->stream, rv, bx);
+    else if (p == QCD_F64) rc = dispatch<QCD_F64>(sc, A, grid, block, c->stream, rv);
+    else if (p == QCD_F32) rc = dispatch<QCD_F32>(sc, A, grid, block, c->stream, rv);
+    else if (p == QCD_DF64) rc = dispatch<QCD_DF64>(sc, A, grid, block, c->stream, rv);
+    else rc = dispatch<QCD_F16>(sc, A, grid, block, c->stream, rv);
     if (rc != QCD_OK) return rc;
     QCD_CUDA_CHECK(cudaGetLastError());
     return QCD_OK;

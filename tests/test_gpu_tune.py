@@ -26,8 +26,16 @@ def test_autotune_cache_and_parity(tmp_path):
     ctx.autotune(cache)
     entries = ctx.tune_info()
     assert len(entries) >= 15
-    assert all(e["threads"] in (32, 64, 128, 256) and e["variant"] in (0, 1) for e in entries)
-    assert all(e["variant"] == 0 for e in entries if e["prec"] == 0)  # no capped FP64 variant
+    def mrhs(e):  # the shared-memory multi-RHS kernel: FP32 hopping / MULT, several RHS
+        return e["prec"] == 1 and e["nrhs"] > 1 and e["red"] == 0 and e["mode"] in (0, 1)
+
+    for e in entries:
+        assert e["variant"] in (0, 1, 2, 3)
+        if mrhs(e):  # threads = right-hand sides per block, a divisor of nrhs; one site per thread
+            assert e["nrhs"] % e["threads"] == 0 and e["variant"] & 2 == 0
+        else:
+            assert e["threads"] in (32, 64, 128, 256)
+    assert all(e["variant"] & 1 == 0 for e in entries if e["prec"] == 0)  # no capped FP64 variant
     data = json.load(open(cache))
     assert len(data) == len(entries)
     # a second context on the same lattice reads the cache: identical choices
@@ -58,3 +66,65 @@ def test_autotune_cache_and_parity(tmp_path):
     assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
     ctx.close()
     ctx2.close()
+
+
+def test_forced_launch_shapes_keep_parity(tmp_path):
+    """Every tuned entry rewritten to two sites per thread (and the multi-RHS
+    kernel to a tile of 4 right-hand sides); a context that reads that cache
+    runs those shapes, and the operators and a solve still match the oracle."""
+    from paper_1709_08785_gb300 import qcd
+
+    dims, kappa, csw, t_bc = (6, 2, 4, 10), 0.124, 1.6, -1  # Vh = 240: ragged blocks
+    U = inputs.random_gauge(dims, 0.25, 94)
+    cache = str(tmp_path / "tune.json")
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    ctx.autotune(cache)
+    data = json.load(open(cache))
+    for k, (variant, bx, us) in list(data.items()):
+        key = int(k.rsplit("|", 1)[1])
+        prec, mode, red, nrhs = key & 3, (key >> 2) & 7, (key >> 5) & 3, key >> 8
+        if prec == 1 and nrhs > 1 and red == 0 and mode in (0, 1):
+            data[k] = [variant, 4, us]
+        else:
+            data[k] = [variant | 2, 64 if nrhs == 1 else 32, us]
+    # the cache's own layout: one entry per line
+    with open(cache, "w") as f:
+        f.write("{\n" + ",\n".join('  "%s": [%d, %d, %.3f]' % (k, *e) for k, e in data.items()) + "\n}\n")
+    ctx.close()
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    ctx.autotune(cache)
+    assert all((e["variant"] & 2) or e["threads"] == 4 for e in ctx.tune_info())
+    F = oracle.clover_field(dims, U, kappa, csw)
+    Fi = oracle.invert_sites(F)
+    Vh = inputs.volume(dims) // 2
+    v = inputs.gaussian_source(dims, 95)[:Vh]
+    want = oracle.dhat(dims, t_bc, U, Fi, kappa, v)
+    for prec, tol, dt in ((0, 1e-13, torch.complex128), (1, 2e-6, torch.complex64), (2, 2e-3, torch.complex64),
+                          (3, 1e-13, torch.complex128)):
+        inp = torch.from_numpy(v).to(dt).cuda()
+        out = torch.zeros_like(inp)
+        ctx.dhat(out, inp, prec)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol, prec
+    # 12 right-hand sides through the tiled kernel, against single-RHS oracle MULTs
+    vs = np.stack([inputs.gaussian_source(dims, 96 + k)[:Vh] for k in range(12)])
+    inp = torch.from_numpy(vs).to(torch.complex64).cuda()
+    out = torch.zeros_like(inp)
+    ctx.mult_eo(out, inp, 1, False, 1, 12)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.complex128)
+    for k in range(12):
+        wk = oracle.mult(dims, t_bc, U, Fi, 1, vs[k])
+        assert np.linalg.norm(got[k] - wk) / np.linalg.norm(wk) < 2e-6, k
+    b = inputs.gaussian_source(dims, 97)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    info = ctx.solve(bd, x, tol=1e-12, precision_levels=2)
+    assert info["status"] == 0
+    assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
+    ctx.close()
