@@ -1,12 +1,13 @@
-// Batched solves: many independent nested FP64/FP32 solves (Algs. 1-2), each
-// on its own lattice, gauge field and kappa, advanced together by one
-// persistent cooperative kernel per outer half-step:
+// Batched solves: many independent nested solves (Algs. 1-2), each on its
+// own lattice, gauge field and kappa, advanced together by two persistent
+// cooperative kernels per outer half-step:
 //
-//   inner level (FP32, Alg. 2, every problem to its own exit):
+//   batched_inner (FP32, Alg. 2, every problem to its own exit):
 //     init | { MULT | D^ 2nd half + <r~|q> | alpha | s = r - a q, |s| | exit? |
 //              MULT | D^ 2nd half + <t|s>,|t|^2 | omega | x, r, <r~|r> | beta, exit? | p }
-//   lift v = |src| x (FP64) | outer D^ (FP64) with its dot | alpha or omega |
-//   outer update and exit test | (second half-step) p update
+//     | lift v = |src| x into the outer precision
+//   batched_outer (DF64 by default, FP64 on request): outer D^ with its dot |
+//     alpha or omega | outer update and exit test | (second half-step) p update
 //
 // Each phase walks work tiles (256 sites of one parity of one problem)
 // across all lattices; tiles of problems that have finished are skipped.
@@ -14,9 +15,11 @@
 // adds them in tile order (deterministic) and runs the BiCGStab scalar
 // recurrences of that problem.  Phases are separated by a grid barrier whose
 // waits are bounded: a barrier that does not complete within the spin limit
-// records QCD_ETIMEOUT and every block returns.  The two half-steps of an
-// outer iteration are captured once in a CUDA graph and replayed until every
-// problem has converged.
+// records QCD_ETIMEOUT and every block returns.  The two kernels exist
+// because their register needs differ (~80 for the FP32 phases, ~170 for
+// the float-pair arithmetic): one kernel held the FP32 phases to one block
+// per SM.  The four launches of an outer iteration are captured once in a
+// CUDA graph and replayed until every problem has converged.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -32,7 +35,7 @@ namespace {
 
 constexpr int TILE = 256;  // sites per work tile = threads per block
 // spinors written and read inside one launch: coherent loads (see Prec)
-constexpr int C32 = QCD_F32 + COHERENT, C64 = QCD_F64 + COHERENT;
+constexpr int C32 = QCD_F32 + COHERENT, C64 = QCD_F64 + COHERENT, CDF = QCD_DF64 + COHERENT;
 constexpr int STATE_WORDS = sizeof(SolverState) / sizeof(double);
 static_assert(sizeof(SolverState) % sizeof(double) == 0, "SolverState is copied as doubles");
 
@@ -44,10 +47,10 @@ struct BProb {
     Geom g;
     double k2;  // kappa^2
     float k2f;  // kappa^2 rounded to FP32 on the host, for the FP32 phases
-    GaugePtr U32, U64;
-    CloverPtr Ci32, Ci64;
+    GaugePtr U32, UO;
+    CloverPtr Ci32, CiO;                       // UO, CiO: in the outer level's precision
     SpinorPtr x, r, rt, p, q, t, tmp;          // FP32 inner (tmp: odd parity)
-    SpinorPtr X, R, RT, P, Q, T, Vv, TMP;      // FP64 outer
+    SpinorPtr X, R, RT, P, Q, T, Vv, TMP;      // outer level: DF64 (default) or FP64
     SolverState *in, *out;                     // inner, outer scalars
     double *partials;                          // [ntiles][4]
     int tile0, ntiles;
@@ -135,9 +138,26 @@ enum Phase {
     PH_LIFT, PH_OMULT, PH_ODHAT, PH_OUPD, PH_OP
 };
 
-// one phase over all tiles of all live problems
+// the outer level's hopping term: the rolled loops for DF64 (instruction cache)
+template <int PO>
+__device__ __forceinline__ void hop_outer(const BProb &pr, const SpinorPtr &in, int out_par, int cb,
+                                          Spinor<typename Prec<PO>::T> &a)
+{
+    if constexpr (PO == CDF) {
+        hopping_rolled<PO, false>(pr.g, pr.UO, in, out_par, cb, a);
+        apply_clover_rolled<PO>(pr.CiO, out_par, cb, a);
+    } else {
+        hopping<PO, false>(pr.g, pr.UO, in, out_par, cb, a);
+        apply_clover<PO>(pr.CiO, out_par, cb, a);
+    }
+}
+
+// one phase over all tiles of all live problems; PO: the outer level's
+// (coherent) precision, DF64 or FP64
+template <int PO, bool OUTER>
 __device__ void run_phase(const BatchArgs &A, int ph)
 {
+    using TO = typename Prec<PO>::T;
     for (int tile = blockIdx.x; tile < A.total_tiles; tile += gridDim.x) {
         const int pi = find_prob(A, tile);
         const BProb &pr = A.probs[pi];
@@ -164,13 +184,15 @@ __device__ void run_phase(const BatchArgs &A, int ph)
         bool f32red = false;
         switch (ph) {
         case PH_INIT: {  // b = src/|src|, r = r~ = p = b, x = 0 (src: p or r of the outer level)
+            if constexpr (OUTER) break;
             const SpinorPtr src = A.half == 0 ? pr.P : pr.R;
             const double *n2 = A.half == 0 ? &s_out.norm2[1] : &s_out.rr;
-            if (in_range) OpInner<C64, C32>{src, pr.r, pr.rt, pr.p, pr.x, n2}(cb, acc);
+            if (in_range) OpInner<PO, C32>{src, pr.r, pr.rt, pr.p, pr.x, n2}(cb, acc);
             break;
         }
         case PH_MULT_P:
         case PH_MULT_S:
+            if constexpr (OUTER) break;
             if (site) {
                 Spinor<float> a;
                 hopping<C32, false>(pr.g, pr.U32, ph == PH_MULT_P ? pr.p : pr.r, 1, cb, a);
@@ -180,6 +202,7 @@ __device__ void run_phase(const BatchArgs &A, int ph)
             break;
         case PH_DHAT_Q:
         case PH_DHAT_T:
+            if constexpr (OUTER) break;
             if (site) {
                 Spinor<float> a, y;
                 hopping<C32, false>(pr.g, pr.U32, pr.tmp, 0, cb, a);
@@ -201,63 +224,69 @@ __device__ void run_phase(const BatchArgs &A, int ph)
             f32red = true;
             break;
         case PH_S:
+            if constexpr (OUTER) break;
             if (in_range) OpS<C32>{pr.r, pr.q, &s_in}(cb, accf);
             nred = 1;
             f32red = true;
             break;
         case PH_X:
+            if constexpr (OUTER) break;
             if (in_range) OpX<C32>{pr.x, pr.p, pr.r, pr.t, pr.rt, &s_in}(cb, accf);
             nred = 3;
             f32red = true;
             break;
         case PH_P:
+            if constexpr (OUTER) break;
             if (in_range) OpP<C32>{pr.p, pr.r, pr.q, &s_in}(cb, accf);
             break;
         case PH_LIFT:  // finish the inner solve: x += alpha p after a first-half exit; v = |src| x
+            if constexpr (OUTER) break;
             if (in_range) {
                 OpHalf<C32>{pr.x, pr.p, &s_in}(cb, acc);
                 const double *n2 = A.half == 0 ? &s_out.norm2[1] : &s_out.rr;
-                OpLift<C32, C64>{pr.x, pr.Vv, n2}(cb, acc);
+                OpLift<C32, PO>{pr.x, pr.Vv, n2}(cb, acc);
             }
             break;
         case PH_OMULT:
+            if constexpr (!OUTER) break;
             if (site) {
-                Spinor<double> a;
-                hopping<C64, false>(pr.g, pr.U64, pr.Vv, 1, cb, a);
-                apply_clover<C64>(pr.Ci64, 1, cb, a);
-                Prec<C64>::store(pr.TMP, cb, a);
+                Spinor<TO> a;
+                hop_outer<PO>(pr, pr.Vv, 1, cb, a);
+                Prec<PO>::store(pr.TMP, cb, a);
             }
             break;
         case PH_ODHAT:
+            if constexpr (!OUTER) break;
             if (site) {
-                Spinor<double> a, v;
-                hopping<C64, false>(pr.g, pr.U64, pr.TMP, 0, cb, a);
-                apply_clover<C64>(pr.Ci64, 0, cb, a);
-                Prec<C64>::load(pr.Vv, cb, v);
-                axpby_sp(a, -pr.k2, a, 1.0, v);
-                Prec<C64>::store(A.half == 0 ? pr.Q : pr.T, cb, a);
+                Spinor<TO> a, v;
+                hop_outer<PO>(pr, pr.TMP, 0, cb, a);
+                Prec<PO>::load(pr.Vv, cb, v);
+                axpby_sp(a, TO(-pr.k2), a, TO(1.0), v);
+                Prec<PO>::store(A.half == 0 ? pr.Q : pr.T, cb, a);
                 if (A.half == 0) {
-                    Spinor<double> w;
-                    Prec<C64>::load(pr.RT, cb, w);
-                    dot_sp(w, a, acc[0], acc[1]);
+                    Spinor<TO> w;
+                    Prec<PO>::load(pr.RT, cb, w);
+                    acc_dot(w, a, acc[0], acc[1]);
                 } else {
-                    Spinor<double> rr;
-                    Prec<C64>::load(pr.R, cb, rr);
-                    dot_sp(a, rr, acc[0], acc[1]);
-                    acc[2] += norm2_sp(a);
+                    Spinor<TO> rr;
+                    Prec<PO>::load(pr.R, cb, rr);
+                    acc_dot(a, rr, acc[0], acc[1]);
+                    acc_norm2(acc[2], a);
                 }
             }
             nred = 3;
             break;
         case PH_OUPD:
+            if constexpr (!OUTER) break;
             if (in_range) {
-                if (A.half == 0) OpFlex1<C64>{pr.X, pr.Vv, pr.R, pr.Q, &s_out}(cb, acc);
-                else OpFlex2<C64>{pr.X, pr.Vv, pr.R, pr.T, pr.RT, &s_out}(cb, acc);
+                if (A.half == 0) OpFlex1<PO>{pr.X, pr.Vv, pr.R, pr.Q, &s_out}(cb, acc);
+                else OpFlex2<PO>{pr.X, pr.Vv, pr.R, pr.T, pr.RT, &s_out}(cb, acc);
             }
             nred = 3;
             break;
         case PH_OP:
-            if (in_range) OpP<C64>{pr.P, pr.R, pr.Q, &s_out}(cb, acc);
+            if constexpr (!OUTER) break;
+            if (in_range) OpP<PO>{pr.P, pr.R, pr.Q, &s_out}(cb, acc);
             nred = 1;
             break;
         }
@@ -339,63 +368,72 @@ __device__ void inner_account(const BatchArgs &A)
     }
 }
 
-__global__ void __launch_bounds__(TILE) batched_halfstep(BatchArgs A)
-{
-#define SYNC()                           \
-    do {                                 \
-        if (!grid_barrier(A)) return;    \
+// One outer half-step is two cooperative launches: the inner FP32 solve
+// (Alg. 2) of every live problem, with the conversions between the levels,
+// at FP32-kernel occupancy; then the outer D^ and updates (Alg. 1) in PO,
+// whose float-pair or FP64 arithmetic needs about twice the registers.
+#define QCD_SYNC()                    \
+    do {                              \
+        if (!grid_barrier(A)) return; \
     } while (0)
+template <int PO>
+__global__ void __launch_bounds__(TILE, 3) batched_inner(BatchArgs A)
+{
     inner_start(A);
-    run_phase(A, PH_INIT);
-    SYNC();
+    run_phase<PO, false>(A, PH_INIT);
+    QCD_SYNC();
     for (int it = 0; it <= A.inner_maxit; ++it) {
-        run_phase(A, PH_MULT_P);
-        SYNC();
-        run_phase(A, PH_DHAT_Q);
-        SYNC();
+        run_phase<PO, false>(A, PH_MULT_P);
+        QCD_SYNC();
+        run_phase<PO, false>(A, PH_DHAT_Q);
+        QCD_SYNC();
         run_finalise(A, PH_DHAT_Q);
-        SYNC();
-        run_phase(A, PH_S);
-        SYNC();
+        QCD_SYNC();
+        run_phase<PO, false>(A, PH_S);
+        QCD_SYNC();
         run_finalise(A, PH_S);
-        SYNC();
-        run_phase(A, PH_MULT_S);
-        SYNC();
-        run_phase(A, PH_DHAT_T);
-        SYNC();
+        QCD_SYNC();
+        run_phase<PO, false>(A, PH_MULT_S);
+        QCD_SYNC();
+        run_phase<PO, false>(A, PH_DHAT_T);
+        QCD_SYNC();
         run_finalise(A, PH_DHAT_T);
-        SYNC();
-        run_phase(A, PH_X);
-        SYNC();
+        QCD_SYNC();
+        run_phase<PO, false>(A, PH_X);
+        QCD_SYNC();
         run_finalise(A, PH_X);
-        SYNC();
-        run_phase(A, PH_P);
-        SYNC();
+        QCD_SYNC();
+        run_phase<PO, false>(A, PH_P);
+        QCD_SYNC();
         bool any = false;
         for (int pi = 0; pi < A.nprob && !any; ++pi)
             any = !__ldcg(&A.probs[pi].out->done) && !__ldcg(&A.probs[pi].in->done);
         if (!any) break;
     }
     inner_account(A);
-    run_phase(A, PH_LIFT);
-    SYNC();
-    run_phase(A, PH_OMULT);
-    SYNC();
-    run_phase(A, PH_ODHAT);
-    SYNC();
+    run_phase<PO, false>(A, PH_LIFT);
+}
+
+template <int PO>
+__global__ void __launch_bounds__(TILE) batched_outer(BatchArgs A)
+{
+    run_phase<PO, true>(A, PH_OMULT);
+    QCD_SYNC();
+    run_phase<PO, true>(A, PH_ODHAT);
+    QCD_SYNC();
     run_finalise(A, PH_ODHAT);
-    SYNC();
-    run_phase(A, PH_OUPD);
-    SYNC();
+    QCD_SYNC();
+    run_phase<PO, true>(A, PH_OUPD);
+    QCD_SYNC();
     run_finalise(A, PH_OUPD);
     if (A.half == 1) {
-        SYNC();
-        run_phase(A, PH_OP);
-        SYNC();
+        QCD_SYNC();
+        run_phase<PO, true>(A, PH_OP);
+        QCD_SYNC();
         run_finalise(A, PH_OP);
     }
-#undef SYNC
 }
+#undef QCD_SYNC
 
 SpinorPtr sp(const HVec &v) { return v.sp(); }
 
@@ -406,6 +444,11 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
 {
     qcd_ctx *c0 = ctxs[0];
     cudaStream_t user = c0->stream;
+    // the outer level in DF64 (float pairs) unless FP64 is asked for, as in
+    // the single solve; the true residual is FP64 either way
+    const int PO = o.outer_df64 ? QCD_DF64 : QCD_F64;
+    void (*kin)(BatchArgs) = o.outer_df64 ? batched_inner<CDF> : batched_inner<C64>;
+    void (*kout)(BatchArgs) = o.outer_df64 ? batched_outer<CDF> : batched_outer<C64>;
     std::vector<BProb> host(n);
     int tiles = 0;
     // ---- per problem: b^_e, |b|^2, and the outer start (same steps as the single solve)
@@ -419,13 +462,15 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
             set_error_message("problem %d: no clover term", i);
             return QCD_ESTATE;
         }
-        HVec be, bo, bh, L64[8], L32[8];
+        // FP64 b_e, b_o (norms, true residual); the outer level in PO
+        HVec be, bo, beO, boO, bh, LO[8], L32[8];
         int rc;
         if ((rc = get_work(c, QCD_F64, S64_BE, &be)) || (rc = get_work(c, QCD_F64, S64_BO, &bo)) ||
-            (rc = get_work(c, QCD_F64, S64_BHAT, &bh)))
+            (rc = get_work(c, PO, S64_BE, &beO)) || (rc = get_work(c, PO, S64_BO, &boO)) ||
+            (rc = get_work(c, PO, S64_BHAT, &bh)))
             return rc;
         for (int k = 0; k < 8; ++k)
-            if ((rc = get_work(c, QCD_F64, S64_LEVEL + k, &L64[k])) || (rc = get_work(c, QCD_F32, S32_LEVEL + k, &L32[k])))
+            if ((rc = get_work(c, PO, S64_LEVEL + k, &LO[k])) || (rc = get_work(c, QCD_F32, S32_LEVEL + k, &L32[k])))
                 return rc;
         SolverState *outer = c->states + ST_OUTER, *inner = c->states + ST_MID, *aux = c->states + ST_AUX;
         const int nn = c->g.Vh_pad;
@@ -436,22 +481,24 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         if (!rc) rc = state_init(c, aux, 0.0, 0.0, 0, 0.0, 0);
         if (!rc) rc = blas_norm2(c, QCD_F64, nn, be, aux, FIN_SETN + 0);
         if (!rc) rc = blas_norm2(c, QCD_F64, nn, bo, aux, FIN_ADDN + 0);
-        if (!rc) rc = clover_apply_half(c, QCD_F64, 1, 1, bo, L64[7], 1, 0);
+        if (!rc && PO != QCD_F64) rc = convert_half(c, be, beO);
+        if (!rc && PO != QCD_F64) rc = convert_half(c, bo, boO);
+        if (!rc) rc = clover_apply_half(c, PO, 1, 1, boO, LO[7], 1, 0);
         if (!rc) {
             StencilCall s;
-            s.prec = QCD_F64;
+            s.prec = PO;
             s.mode = M_SRC;
             s.out_par = 0;
             s.out = bh;
-            s.in = L64[7];
-            s.y = be;
+            s.in = LO[7];
+            s.y = beO;
             s.a = 1.0;
             s.cc = c->kappa;
             rc = launch_stencil(c, s);
         }
         if (!rc) rc = state_init(c, outer, 0.0, 0.0, o.max_outer, 1e-30, 0);
         if (!rc) rc = set_tol2(c, outer, aux, 0, 0.25 * tol[i] * tol[i]);
-        if (!rc) rc = blas_init(c, QCD_F64, nn, bh, L64[1], L64[2], L64[3], L64[0], 1, outer, FIN_INIT);
+        if (!rc) rc = blas_init(c, PO, nn, bh, LO[1], LO[2], LO[3], LO[0], 1, outer, FIN_INIT);
         c->stream = keep;
         if (rc) return rc;
         BProb &pr = host[i];
@@ -461,15 +508,15 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         for (int par = 0; par < 2; ++par) {
             pr.U32.a[par] = c->U32[par];
             pr.U32.b[par] = nullptr;
-            pr.U64.a[par] = c->U64[par];
-            pr.U64.b[par] = nullptr;
+            pr.UO.a[par] = PO == QCD_DF64 ? (const void *)c->UDF[par] : (const void *)c->U64[par];
+            pr.UO.b[par] = nullptr;
             pr.Ci32.p[par] = c->Ci[QCD_F32][par];
-            pr.Ci64.p[par] = c->Ci[QCD_F64][par];
+            pr.CiO.p[par] = c->Ci[PO][par];
         }
         pr.x = sp(L32[0]); pr.r = sp(L32[1]); pr.rt = sp(L32[2]); pr.p = sp(L32[3]);
         pr.q = sp(L32[4]); pr.t = sp(L32[5]); pr.tmp = sp(L32[7]);
-        pr.X = sp(L64[0]); pr.R = sp(L64[1]); pr.RT = sp(L64[2]); pr.P = sp(L64[3]);
-        pr.Q = sp(L64[4]); pr.T = sp(L64[5]); pr.Vv = sp(L64[6]); pr.TMP = sp(L64[7]);
+        pr.X = sp(LO[0]); pr.R = sp(LO[1]); pr.RT = sp(LO[2]); pr.P = sp(LO[3]);
+        pr.Q = sp(LO[4]); pr.T = sp(LO[5]); pr.Vv = sp(LO[6]); pr.TMP = sp(LO[7]);
         pr.in = inner;
         pr.out = outer;
         pr.partials = c->partials;
@@ -503,13 +550,16 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
     QCD_CUDA_CHECK(cudaMemcpyAsync(dprobs, host.data(), pbytes, cudaMemcpyHostToDevice, user));
     QCD_CUDA_CHECK(cudaMemsetAsync(bar, 0, 64, user));
 
-    int per_sm = 0;
-    QCD_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_halfstep, TILE, 0));
-    if (per_sm < 1) {
-        set_error_message("the batched kernel cannot be resident");
+    // cooperative grids: every block of a launch resident at once
+    int per_in = 0, per_out = 0;
+    QCD_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_in, kin, TILE, 0));
+    QCD_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_out, kout, TILE, 0));
+    if (per_in < 1 || per_out < 1) {
+        set_error_message("the batched kernels cannot be resident");
         return QCD_ECUDA;
     }
-    const int grid = std::max(1, std::min(tiles, per_sm * c0->num_sms));
+    const int grid_in = std::max(1, std::min(tiles, per_in * c0->num_sms));
+    const int grid_out = std::max(1, std::min(tiles, per_out * c0->num_sms));
     BatchArgs A[2];
     for (int h = 0; h < 2; ++h) {
         A[h].probs = dprobs;
@@ -530,7 +580,7 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
     QCD_CUDA_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     QCD_CUDA_CHECK(cudaEventRecord(ev, user));
     QCD_CUDA_CHECK(cudaStreamWaitEvent(s, ev, 0));
-    auto launch = [&](int h) -> cudaError_t {
+    auto launch1 = [&](void (*k)(BatchArgs), int grid, int h) -> cudaError_t {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(TILE);
@@ -540,7 +590,11 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, batched_halfstep, A[h]);
+        return cudaLaunchKernelEx(&cfg, k, A[h]);
+    };
+    auto launch = [&](int h) -> cudaError_t {
+        const cudaError_t e = launch1(kin, grid_in, h);
+        return e != cudaSuccess ? e : launch1(kout, grid_out, h);
     };
     cudaGraphExec_t exec = nullptr;
     int graph_used = 0;
@@ -560,7 +614,7 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
     int status = QCD_OK;
     int outer_done = 0;
     for (int it = 0; it < o.max_outer && !outer_done; ++it) {
-        c0->launches += 2;
+        c0->launches += 4;
         if (graph_used) {
             QCD_CUDA_CHECK(cudaGraphLaunch(exec, s));
         } else {
@@ -594,24 +648,30 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         qcd_ctx *c = ctxs[i];
         cudaStream_t keep = c->stream;
         c->stream = user;
-        HVec be, bo, xo, re, ro, X;
+        // x_o = F_oo^-1 (b_o + kappa H_oe x_e) in the outer precision, then
+        // x rounded to FP64 for the FP64 true residual
+        HVec be, bo, xo, re, ro, X, XO, xoO, boO;
         int r = QCD_OK;
         if ((r = get_work(c, QCD_F64, S64_BE, &be)) || (r = get_work(c, QCD_F64, S64_BO, &bo)) ||
             (r = get_work(c, QCD_F64, S64_XO, &xo)) || (r = get_work(c, QCD_F64, S64_RE, &re)) ||
-            (r = get_work(c, QCD_F64, S64_RO, &ro)) || (r = get_work(c, QCD_F64, S64_LEVEL, &X))) {
+            (r = get_work(c, QCD_F64, S64_RO, &ro)) || (r = get_work(c, QCD_F64, S64_LEVEL, &X)) ||
+            (r = get_work(c, PO, S64_LEVEL, &XO)) || (r = get_work(c, PO, S64_XO, &xoO)) ||
+            (r = get_work(c, PO, S64_BO, &boO))) {
             c->stream = keep;
             return r;
         }
         StencilCall sx;
-        sx.prec = QCD_F64;
+        sx.prec = PO;
         sx.mode = M_SRC;
         sx.out_par = 1;
-        sx.out = xo;
-        sx.in = X;
-        sx.y = bo;
+        sx.out = xoO;
+        sx.in = XO;
+        sx.y = boO;
         sx.a = 1.0;
         sx.cc = c->kappa;
         r = launch_stencil(c, sx);
+        if (!r && PO != QCD_F64) r = convert_half(c, XO, X);
+        if (!r && PO != QCD_F64) r = convert_half(c, xoO, xo);
         for (int par = 0; par < 2 && !r; ++par) {
             StencilCall sr;
             sr.prec = QCD_F64;

@@ -547,6 +547,16 @@ struct Prec<QCD_F32 + COHERENT> : Prec<QCD_F32> {
     }
 };
 
+template <>
+struct Prec<QCD_DF64 + COHERENT> : Prec<QCD_DF64> {
+    static __device__ __forceinline__ void load(const SpinorPtr &v, int cb, Spinor<T> &s)
+    {
+        const float4 *p = (const float4 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s.s[k / 3][k % 3] = f4c(__ldcg(p + soa(cb, 12, k)));
+    }
+};
+
 // ---------------------------------------------------------------- clover
 // y = A x for a 6x6 Hermitian block (d real diagonal, o lower triangle,
 // row-major: o[0]=(1,0), o[1]=(2,0), o[2]=(2,1), o[3]=(3,0), ...).
