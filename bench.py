@@ -38,7 +38,8 @@ WORKLOAD_NAME = ("24^3x48 clover-Wilson, even-odd preconditioned nested BiCGStab
                  "Gaussian source seed 30, tol 1e-12")
 # algorithmic bytes per output site of the FP32 stencil kernels of one D^:
 # MULT (in 96 + links 8x48 + clover 288 + out 96) and the fused second half
-STENCIL_SOURCES = ["paper_1709_08785_gb300/csrc/stencil.cu", "paper_1709_08785_gb300/csrc/qcd_internal.cuh",
+STENCIL_SOURCES = ["paper_1709_08785_gb300/csrc/stencil_impl.cuh", "paper_1709_08785_gb300/csrc/stencil.cuh",
+                   "paper_1709_08785_gb300/csrc/stencil_f32.cu", "paper_1709_08785_gb300/csrc/qcd_internal.cuh",
                    "paper_1709_08785_gb300/csrc/reduce.cuh"]
 TUNE_CACHE = os.path.join(ROOT, "paper_1709_08785_gb300", "_build", "tune_cache.json")
 

@@ -274,8 +274,8 @@ int qcd_reset_kernel_stats(qcd_ctx *ctx);
 long qcd_launch_count(const qcd_ctx *ctx);
 
 /* Autotune the launch configurations of the operator kernels the solvers
- * use (register budget, sites per thread and threads per block -- or, for
- * the multi-RHS kernel, right-hand sides per block -- for each precision,
+ * use (register budget and threads per block -- or, for the multi-RHS
+ * kernel, right-hand sides per block -- for each precision,
  * fused reduction and right-hand-side count): every candidate is timed on scratch
  * buffers, with L2 evicted, and the fastest kept for this context.  If
  * cache_path is not NULL the choices are read from and added to that JSON
@@ -284,11 +284,11 @@ long qcd_launch_count(const qcd_ctx *ctx);
  * Synchronous. */
 int qcd_autotune(qcd_ctx *ctx, const char *cache_path);
 
-/* The tuned configurations: up to max entries (key; variant, bit 0 the
- * capped register budget and bit 1 two sites per thread; threads per block
- * along the sites, or right-hand sides per block for the multi-RHS kernel;
- * microseconds per launch); returns the number of entries held. Any output
- * pointer may be NULL. */
+/* The tuned configurations: up to max entries (key; variant, 1 for the
+ * capped register budget; threads per block along the sites, or
+ * right-hand sides per block for the multi-RHS kernel; microseconds per
+ * launch); returns the number of entries held. Any output pointer may be
+ * NULL. */
 int qcd_tune_info(qcd_ctx *ctx, int max, unsigned *keys, int *variant, int *threads, double *us);
 
 /* Time the fused MULT kernel (Sec. II-B, out = F^-1 H_{p,1-p} in) alone on

@@ -303,7 +303,6 @@ struct StencilArgs {
     const int *done;
     int *skip;  // profiling: set to 1 when the launch returns early
     int nrhs;   // right-hand sides of the launch (multi-RHS: blockIdx.y selects a tile of them)
-    int spt;    // output sites per thread (1 or 2)
 };
 
 // a host-supplied scalar in the kernel's arithmetic type (float: the

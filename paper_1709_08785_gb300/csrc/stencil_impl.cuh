@@ -1,0 +1,198 @@
+// The hopping stencil H_{p,1-p} (Eq. 4) and the kernels built on it (the
+// kernel templates; one translation unit per precision instantiates them):
+//   M_HOP   out = H in                       (qcd_dslash_eo)
+//   M_MULT  out = F^-1 H in                  (MULT = H~, Sec. II-B)
+//   M_DHAT  out = a*y + cc*F^-1 H in + d*z   (second half of D^ = 1 - k^2 H~_eo H~_oe,
+//                                             with the dot products of Alg. 2 fused)
+//   M_SRC   out = F^-1 (a*y + cc*H in)       (b^_e, Eq. 6, and x_o, Eq. 7)
+//   M_FULL  out = a*F y + cc*H in + d*z      (D = F - kappa H on one parity, residuals)
+//
+// One thread computes one output site (and one right-hand side: the
+// right-hand sides of a site sit in the same block so that its links and
+// clover entries are fetched from HBM once and hit L1 for the others).
+// For each of the 8 directions the neighbour spinor is projected with
+// (1 -/+ gamma_mu) to two spin components before the colour multiply
+// (the rank-2 structure of Eq. 4), the link is rebuilt from 12 reals for
+// FP32/FP16 (Sec. III-A), multiplied, and expanded back.
+#pragma once
+
+#include "stencil.cuh"
+
+namespace qcd {
+
+// One output site cb (right-hand side r): the hops, the mode's epilogue, the
+// site's contributions to the fused reductions.
+template <int P, int MODE, int RED, bool DAG, class RA>
+__device__ __forceinline__ void stencil_site(const StencilArgs &A, int cb, int r, RA red[4])
+{
+    using T = typename Prec<P>::T;
+    const SpinorPtr in = rhs_ptr(A.in, r, A.rhs_stride, A.norm_stride);
+    const SpinorPtr out = rhs_ptr(A.out, r, A.rhs_stride, A.norm_stride);
+    Spinor<T> acc;
+    hopping_any<P, DAG>(A.g, A.U, in, A.out_par, cb, acc);
+    if (MODE == M_MULT) {
+        clover_any<P>(A.C,A.out_par, cb, acc);
+    } else if (MODE == M_DHAT) {
+        clover_any<P>(A.C,A.out_par, cb, acc);
+        Spinor<T> y;
+        Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
+        axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
+        if (A.has_z) {
+            Spinor<T> z;
+            Prec<P>::load(rhs_ptr(A.z, r, A.rhs_stride, A.norm_stride), cb, z);
+            axpby_sp(acc, T(1), acc, sarg<T>(A.d, A.df32), z);
+        }
+        if (RED == R_OMEGA) {  // <out|aux>, |out|^2 (aux is usually y)
+            if (A.aux.p != A.y.p) Prec<P>::load(rhs_ptr(A.aux, r, A.rhs_stride, A.norm_stride), cb, y);
+            T dr = 0, di = 0, nn = 0;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const cx<T> o = acc.s[s][i], v = y.s[s][i];
+                    dr += o.r * v.r + o.i * v.i;
+                    di += o.r * v.i - o.i * v.r;
+                    nn += o.r * o.r + o.i * o.i;
+                }
+            red[0] += acc_cast<RA>(dr);
+            red[1] += acc_cast<RA>(di);
+            red[2] += acc_cast<RA>(nn);
+        }
+    } else if (MODE == M_SRC) {
+        Spinor<T> y;
+        Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
+        axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
+        clover_any<P>(A.C,A.out_par, cb, acc);
+    } else if (MODE == M_FULL) {
+        Spinor<T> y;
+        Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
+        clover_any<P>(A.C,A.out_par, cb, y);
+        axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
+        if (A.has_z) {
+            Spinor<T> z;
+            Prec<P>::load(rhs_ptr(A.z, r, A.rhs_stride, A.norm_stride), cb, z);
+            axpby_sp(acc, T(1), acc, sarg<T>(A.d, A.df32), z);
+        }
+    }
+    if (RED == R_DOT_AUX) {  // <aux|out>
+        Spinor<T> w;
+        Prec<P>::load(rhs_ptr(A.aux, r, A.rhs_stride, A.norm_stride), cb, w);
+        T dr = 0, di = 0;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const cx<T> a = w.s[s][i], o = acc.s[s][i];
+                dr += a.r * o.r + a.i * o.i;
+                di += a.r * o.i - a.i * o.r;
+            }
+        red[0] += acc_cast<RA>(dr);
+        red[1] += acc_cast<RA>(di);
+    } else if (RED == R_NORM) {
+        T nn = 0;
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) nn += acc.s[s][i].r * acc.s[s][i].r + acc.s[s][i].i * acc.s[s][i].i;
+        red[0] += acc_cast<RA>(nn);
+    }
+    Prec<P>::store(out, cb, acc);
+}
+
+template <int P, int MODE, int RED, bool DAG>
+__device__ __forceinline__ void stencil_body(const StencilArgs &A)
+{
+    pdl_enter();
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0;
+    if (A.done && *A.done) {
+        if (A.skip && lead) *A.skip = 1;
+        return;
+    }
+    if (A.skip && lead) *A.skip = 0;
+    const int r = threadIdx.y;
+    // reduction type: float at the FP32 / FP16 levels (see grid_reduce)
+    using RA = typename std::conditional<P == QCD_F32 || P == QCD_F16, float, double>::type;
+    RA red[4] = {RA(0), RA(0), RA(0), RA(0)};
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cb < A.g.Vh) stencil_site<P, MODE, RED, DAG>(A, cb, r, red);
+    if constexpr (RED != R_NONE) grid_reduce<RED == R_OMEGA ? 3 : RED == R_DOT_AUX ? 2 : 1>(red, A.red);
+}
+
+// Two register budgets of the same kernel; the autotuner picks one per
+// launch configuration.  The default lets the compiler use what it needs
+// (384 threads per block at most); the capped one trades a few spills for
+// more resident warps, i.e. more loads in flight.
+template <int P, int MODE, int RED, bool DAG>
+__global__ void __launch_bounds__(384) stencil_kernel(StencilArgs A)
+{
+    stencil_body<P, MODE, RED, DAG>(A);
+}
+
+template <int P, int MODE, int RED, bool DAG>
+__global__ void __maxnreg__(80) stencil_kernel_r80(StencilArgs A)
+{
+    stencil_body<P, MODE, RED, DAG>(A);
+}
+
+// DF64 (arithmetic-bound, ~165 registers by default): a 128-register cap
+// gives four 128-thread blocks per SM instead of three
+template <int P, int MODE, int RED, bool DAG>
+__global__ void __maxnreg__(128) stencil_kernel_r128(StencilArgs A)
+{
+    stencil_body<P, MODE, RED, DAG>(A);
+}
+
+// ---- host launcher -------------------------------------------------------
+template <int P, int MODE, int RED, bool DAG>
+static void launch_t(const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int variant)
+{
+    if constexpr (P == QCD_F32 || P == QCD_F16) {
+        if (variant == 1) {
+            launch_pdl(stencil_kernel_r80<P, MODE, RED, DAG>, grid, block, 0, s, A);
+            return;
+        }
+    }
+    if constexpr (P == QCD_DF64) {
+        if (variant == 1) {
+            launch_pdl(stencil_kernel_r128<P, MODE, RED, DAG>, grid, block, 0, s, A);
+            return;
+        }
+    }
+    launch_pdl(stencil_kernel<P, MODE, RED, DAG>, grid, block, 0, s, A);
+}
+
+template <int P>
+int dispatch(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int v)
+{
+#define QCD_CASE(MODE, RED)                                                   \
+    if (sc.mode == MODE && sc.red == RED) {                                   \
+        if (sc.dagger) launch_t<P, MODE, RED, true>(A, grid, block, s, v);    \
+        else launch_t<P, MODE, RED, false>(A, grid, block, s, v);             \
+        return QCD_OK;                                                        \
+    }
+    QCD_CASE(M_HOP, R_NONE)
+    QCD_CASE(M_MULT, R_NONE)
+#undef QCD_CASE
+    if (sc.dagger) {
+        set_error_message("dagger is only available for the hopping and MULT kernels");
+        return QCD_EINVAL;
+    }
+#define QCD_CASE(MODE, RED)                                                   \
+    if (sc.mode == MODE && sc.red == RED) {                                   \
+        launch_t<P, MODE, RED, false>(A, grid, block, s, v);                  \
+        return QCD_OK;                                                        \
+    }
+    QCD_CASE(M_DHAT, R_NONE)
+    QCD_CASE(M_DHAT, R_DOT_AUX)
+    QCD_CASE(M_DHAT, R_OMEGA)
+    QCD_CASE(M_DHAT, R_NORM)
+    QCD_CASE(M_SRC, R_NONE)
+    QCD_CASE(M_SRC, R_NORM)
+    QCD_CASE(M_FULL, R_NONE)
+    QCD_CASE(M_FULL, R_NORM)
+#undef QCD_CASE
+    set_error_message("unsupported stencil mode %d / reduction %d", sc.mode, sc.red);
+    return QCD_EINVAL;
+}
+
+}  // namespace qcd

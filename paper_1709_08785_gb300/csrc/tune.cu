@@ -1,9 +1,8 @@
 // Autotuner for the stencil kernels: for each launch configuration the
 // solvers use (precision, mode, fused reduction, dagger, right-hand sides) it
 // times every candidate -- register budget (compiler's / capped at 80 for FP32
-// and FP16, at 128 for DF64) x one or two sites per thread x threads per
-// block along the sites, or for the multi-RHS kernel x right-hand sides per
-// block (the RHS tile) -- on scratch
+// and FP16, at 128 for DF64) x threads per block along the sites, or for the
+// multi-RHS kernel x right-hand sides per block (the RHS tile) -- on scratch
 // buffers with L2 evicted before each launch, keeps the fastest, and stores
 // the choice in a JSON cache keyed by device name, lattice and configuration.
 // Launches that have no tuned entry use the default (compiler's budget, 128
@@ -141,9 +140,8 @@ int tune_one(qcd_ctx *c, StencilCall s, qcd_ctx::TuneEntry *out)
     s.norm_stride = (size_t)c->g.Vh_pad;
     s.red_args = RedArgs{c->partials, c->counters, c->states + ST_TUNE, FIN_NONE};
     s.done = nullptr;
-    // variant: bit 0 the register cap (FP32, FP16, DF64 only), bit 1 two
-    // sites per thread (not for the multi-RHS kernel)
-    const bool cap = s.prec == QCD_F32 || s.prec == QCD_F16 || s.prec == QCD_DF64;
+    // variant 1: the register cap (FP32, FP16, DF64 only)
+    const int nv = (s.prec == QCD_F32 || s.prec == QCD_F16 || s.prec == QCD_DF64) ? 2 : 1;
     // sites per block; for the multi-RHS kernel the right-hand sides per block
     // (all, a half, a third, a quarter)
     const int bxs1[] = {64, 128, 256}, bxsn[] = {32, 64};
@@ -154,12 +152,11 @@ int tune_one(qcd_ctx *c, StencilCall s, qcd_ctx::TuneEntry *out)
     const int *bxs = mr ? bxst : s.nrhs > 1 ? bxsn : bxs1;
     const int nbx = mr ? nt : s.nrhs > 1 ? 2 : 3;
     qcd_ctx::TuneEntry best{0, 128, 1e30};
-    for (int v = 0; v < 4; ++v)
+    for (int v = 0; v < nv; ++v)
         for (int k = 0; k < nbx; ++k) {
-            if (((v & 1) && !cap) || ((v & 2) && mr)) continue;
             const int bx = bxs[k];
             if (!mr && bx * s.nrhs > 384) continue;
-            if (s.red != R_NONE && (int)nblocks(c->g.Vh, bx * (1 + (v >> 1))) > c->partial_blocks) continue;
+            if (s.red != R_NONE && (int)nblocks(c->g.Vh, bx) > c->partial_blocks) continue;
             s.force_variant = v;
             s.force_bx = bx;
             double us;

@@ -30,12 +30,12 @@ def test_autotune_cache_and_parity(tmp_path):
         return e["prec"] == 1 and e["nrhs"] > 1 and e["red"] == 0 and e["mode"] in (0, 1)
 
     for e in entries:
-        assert e["variant"] in (0, 1, 2, 3)
-        if mrhs(e):  # threads = right-hand sides per block, a divisor of nrhs; one site per thread
-            assert e["nrhs"] % e["threads"] == 0 and e["variant"] & 2 == 0
+        assert e["variant"] in (0, 1)
+        if mrhs(e):  # threads = right-hand sides per block, a divisor of nrhs
+            assert e["nrhs"] % e["threads"] == 0
         else:
             assert e["threads"] in (32, 64, 128, 256)
-    assert all(e["variant"] & 1 == 0 for e in entries if e["prec"] == 0)  # no capped FP64 variant
+    assert all(e["variant"] == 0 for e in entries if e["prec"] == 0)  # no capped FP64 variant
     data = json.load(open(cache))
     assert len(data) == len(entries)
     # a second context on the same lattice reads the cache: identical choices
@@ -69,9 +69,11 @@ def test_autotune_cache_and_parity(tmp_path):
 
 
 def test_forced_launch_shapes_keep_parity(tmp_path):
-    """Every tuned entry rewritten to two sites per thread (and the multi-RHS
-    kernel to a tile of 4 right-hand sides); a context that reads that cache
-    runs those shapes, and the operators and a solve still match the oracle."""
+    """Every tuned entry rewritten to 64 (32 with several right-hand sides)
+    sites per block and, where it exists, the capped register budget, and
+    the multi-RHS kernel to a tile of 4 right-hand sides; a context that
+    reads that cache runs those shapes, and the operators and a solve still
+    match the oracle."""
     from paper_1709_08785_gb300 import qcd
 
     dims, kappa, csw, t_bc = (6, 2, 4, 10), 0.124, 1.6, -1  # Vh = 240: ragged blocks
@@ -88,7 +90,7 @@ def test_forced_launch_shapes_keep_parity(tmp_path):
         if prec == 1 and nrhs > 1 and red == 0 and mode in (0, 1):
             data[k] = [variant, 4, us]
         else:
-            data[k] = [variant | 2, 64 if nrhs == 1 else 32, us]
+            data[k] = [0 if prec == 0 else 1, 64 if nrhs == 1 else 32, us]
     # the cache's own layout: one entry per line
     with open(cache, "w") as f:
         f.write("{\n" + ",\n".join('  "%s": [%d, %d, %.3f]' % (k, *e) for k, e in data.items()) + "\n}\n")
@@ -97,7 +99,7 @@ def test_forced_launch_shapes_keep_parity(tmp_path):
     ctx.gauge_load(torch.from_numpy(U).cuda())
     ctx.clover_build(kappa, csw)
     ctx.autotune(cache)
-    assert all((e["variant"] & 2) or e["threads"] == 4 for e in ctx.tune_info())
+    assert all(e["threads"] in (4, 32, 64) for e in ctx.tune_info())
     F = oracle.clover_field(dims, U, kappa, csw)
     Fi = oracle.invert_sites(F)
     Vh = inputs.volume(dims) // 2
