@@ -409,6 +409,22 @@ struct Prec<QCD_F16> {
             }
         }
     }
+    // the stored halves unscaled; returns the site's norm (psi = norm * halves)
+    static __device__ __forceinline__ float load_raw(const SpinorPtr &v, int cb, Spinor<T> &s)
+    {
+        const uint4 *p = (const uint4 *)v.p;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            uint4 q = __ldg(p + soa(cb, 3, k));
+            unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int c = 4 * k + j;
+                s.s[c / 3][c % 3] = h2c(u2h(w[j]));
+            }
+        }
+        return __ldg(v.norm + cb);
+    }
     static __device__ __forceinline__ void store(const SpinorPtr &v, int cb, const Spinor<T> &s)
     {
         float m = 0.f;

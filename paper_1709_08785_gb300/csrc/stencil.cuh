@@ -66,6 +66,44 @@ __device__ __forceinline__ void expand(Spinor<T> &acc, const cx<T> g[2][3])
     }
 }
 
+// acc += w * expansion of g (w real): the FP16 kernels fold the neighbour's
+// per-site norm (and the time-boundary sign) into the accumulation, one FMA
+// per real where the unscaled form has one add
+template <int MU, int S, class T>
+__device__ __forceinline__ void expand_w(Spinor<T> &acc, const cx<T> g[2][3], T w)
+{
+    const T nw = -w;
+    static_assert(std::is_same<T, float>::value, "FP32 arithmetic of the FP16-storage kernels");
+    auto add = [](cx<T> &a, const cx<T> &b, T f) { a = mk(::fmaf(f, b.r, a.r), ::fmaf(f, b.i, a.i)); };
+    // a += f * (i b) = (a.r - f b.i, a.i + f b.r)
+    auto addi = [](cx<T> &a, const cx<T> &b, T f) { a = mk(::fmaf(-f, b.i, a.r), ::fmaf(f, b.r, a.i)); };
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (MU == 3) {
+            if (S > 0) {
+                add(acc.s[2][i], g[0][i], w);
+                add(acc.s[3][i], g[1][i], w);
+            } else {
+                add(acc.s[0][i], g[0][i], w);
+                add(acc.s[1][i], g[1][i], w);
+            }
+        } else {
+            add(acc.s[0][i], g[0][i], w);
+            add(acc.s[1][i], g[1][i], w);
+            if (MU == 0) {  // lower = -S i (g1, g0)
+                addi(acc.s[2][i], g[1][i], S > 0 ? nw : w);
+                addi(acc.s[3][i], g[0][i], S > 0 ? nw : w);
+            } else if (MU == 1) {  // lower = -S (g1, -g0)
+                add(acc.s[2][i], g[1][i], S > 0 ? nw : w);
+                add(acc.s[3][i], g[0][i], S > 0 ? w : nw);
+            } else {  // lower = -S i (g0, -g1)
+                addi(acc.s[2][i], g[0][i], S > 0 ? nw : w);
+                addi(acc.s[3][i], g[1][i], S > 0 ? w : nw);
+            }
+        }
+    }
+}
+
 // g = U h  or  g = U^dag h, for both spin rows
 template <bool DAG, class T>
 __device__ __forceinline__ void colour_mul(const Link<T> &U, const cx<T> h[2][3], cx<T> g[2][3])
@@ -92,37 +130,55 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugePtr &U, const 
     const int in_par = 1 - out_par;
     {  // forward hop: (1 - SF g_mu) U_mu(n) psi(n + mu)
         const int nb = lex_hop(g, lex, c, MU, +1) >> 1;
+        const bool flip = MU == 3 && g.t_bc < 0 && c[3] == g.L[3] - 1;
         Spinor<T> psi;
-        Prec<P>::load(in, nb, psi);
         cx<T> h[2][3], q[2][3];
-        project<MU, SF>(psi, h);
         Link<T> L;
-        Prec<P>::load_link(U, out_par, cb, MU, L);
-        colour_mul<false>(L, h, q);
-        if (MU == 3 && g.t_bc < 0 && c[3] == g.L[3] - 1) {
+        if constexpr (P == QCD_F16) {  // the neighbour's norm and the boundary sign go into the accumulation
+            const T w = Prec<P>::load_raw(in, nb, psi);
+            project<MU, SF>(psi, h);
+            Prec<P>::load_link(U, out_par, cb, MU, L);
+            colour_mul<false>(L, h, q);
+            expand_w<MU, SF>(acc, q, flip ? -w : w);
+        } else {
+            Prec<P>::load(in, nb, psi);
+            project<MU, SF>(psi, h);
+            Prec<P>::load_link(U, out_par, cb, MU, L);
+            colour_mul<false>(L, h, q);
+            if (flip) {
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int i = 0; i < 3; ++i) q[a][i] = -q[a][i];
+                    for (int i = 0; i < 3; ++i) q[a][i] = -q[a][i];
+            }
+            expand<MU, SF>(acc, q);
         }
-        expand<MU, SF>(acc, q);
     }
     {  // backward hop: (1 + SF g_mu) U_mu(n - mu)^dag psi(n - mu)
         const int nb = lex_hop(g, lex, c, MU, -1) >> 1;
+        const bool flip = MU == 3 && g.t_bc < 0 && c[3] == 0;
         Spinor<T> psi;
-        Prec<P>::load(in, nb, psi);
         cx<T> h[2][3], q[2][3];
-        project<MU, -SF>(psi, h);
         Link<T> L;
-        Prec<P>::load_link(U, in_par, nb, MU, L);
-        colour_mul<true>(L, h, q);
-        if (MU == 3 && g.t_bc < 0 && c[3] == 0) {
+        if constexpr (P == QCD_F16) {
+            const T w = Prec<P>::load_raw(in, nb, psi);
+            project<MU, -SF>(psi, h);
+            Prec<P>::load_link(U, in_par, nb, MU, L);
+            colour_mul<true>(L, h, q);
+            expand_w<MU, -SF>(acc, q, flip ? -w : w);
+        } else {
+            Prec<P>::load(in, nb, psi);
+            project<MU, -SF>(psi, h);
+            Prec<P>::load_link(U, in_par, nb, MU, L);
+            colour_mul<true>(L, h, q);
+            if (flip) {
 #pragma unroll
-            for (int a = 0; a < 2; ++a)
+                for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int i = 0; i < 3; ++i) q[a][i] = -q[a][i];
+                    for (int i = 0; i < 3; ++i) q[a][i] = -q[a][i];
+            }
+            expand<MU, -SF>(acc, q);
         }
-        expand<MU, -SF>(acc, q);
     }
 }
 
