@@ -573,13 +573,27 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         A[h].err = (int *)(bar + 2);
         A[h].spin_limit = spin_limit;
     }
-    // a stream of our own: graph capture is not possible on the legacy stream
-    cudaStream_t s;
-    QCD_CUDA_CHECK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    cudaEvent_t ev;
-    QCD_CUDA_CHECK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    QCD_CUDA_CHECK(cudaEventRecord(ev, user));
-    QCD_CUDA_CHECK(cudaStreamWaitEvent(s, ev, 0));
+    // a stream of our own: graph capture is not possible on the legacy stream.
+    // The stream, the event and the graph are released on every return path;
+    // the user stream waits for the private one before they go.
+    struct Res {
+        cudaStream_t user, s = nullptr;
+        cudaEvent_t ev = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        ~Res()
+        {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (s && ev && cudaEventRecord(ev, s) == cudaSuccess) cudaStreamWaitEvent(user, ev, 0);
+            if (ev) cudaEventDestroy(ev);
+            if (s) cudaStreamDestroy(s);
+        }
+    } res;
+    res.user = user;
+    QCD_CUDA_CHECK(cudaStreamCreateWithFlags(&res.s, cudaStreamNonBlocking));
+    QCD_CUDA_CHECK(cudaEventCreateWithFlags(&res.ev, cudaEventDisableTiming));
+    cudaStream_t s = res.s;
+    QCD_CUDA_CHECK(cudaEventRecord(res.ev, user));
+    QCD_CUDA_CHECK(cudaStreamWaitEvent(s, res.ev, 0));
     auto launch1 = [&](void (*k)(BatchArgs), int grid, int h) -> cudaError_t {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
@@ -596,7 +610,7 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         const cudaError_t e = launch1(kin, grid_in, h);
         return e != cudaSuccess ? e : launch1(kout, grid_out, h);
     };
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t &exec = res.exec;
     int graph_used = 0;
     if (use_graph) {
         cudaGraph_t graph = nullptr;
@@ -637,11 +651,9 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         QCD_CUDA_CHECK(cudaStreamSynchronize(s));
         for (int i = 0; i < n; ++i) outer_done &= st[i].done;
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    QCD_CUDA_CHECK(cudaEventRecord(ev, s));
-    QCD_CUDA_CHECK(cudaStreamWaitEvent(user, ev, 0));
-    cudaEventDestroy(ev);
-    cudaStreamDestroy(s);
+    // the finishing steps below run on the user stream, after the batch
+    QCD_CUDA_CHECK(cudaEventRecord(res.ev, s));
+    QCD_CUDA_CHECK(cudaStreamWaitEvent(user, res.ev, 0));
     if (status != QCD_OK) return status;
     // ---- per problem: x_o, the true residual, a single-solve restart if needed
     for (int i = 0; i < n; ++i) {

@@ -2,11 +2,13 @@
 // scalar updates that its last block performs.
 //
 // Each block reduces its threads' values (warp shuffles, then one warp over
-// the warp sums), writes one partial per block, and takes a ticket; the
-// block that takes the last ticket adds the partials in block order and
-// runs the finaliser on the solver state.  The sum order depends only on the
-// launch shape, so results repeat bit for bit from run to run.  This replaces
-// the paper's MPI_Allreduce of every dot product and norm (Sec. IV-B).
+// the warp sums) and writes one partial per block; all blocks but the last
+// count themselves with a release add and retire, and the highest-indexed
+// block (dispatched last) waits, bounded, for that count, adds the partials
+// in block order and runs the finaliser on the solver state.  The sum order
+// depends only on the launch shape, so results repeat bit for bit from run
+// to run.  This replaces the paper's MPI_Allreduce of every dot product and
+// norm (Sec. IV-B).
 #pragma once
 
 #include "ctx.cuh"
@@ -160,14 +162,36 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < N; ++k) ra.partials[(size_t)blockIdx.x * 4 + k] = bsum[k];
-            __threadfence();
-            unsigned t = atomicAdd(ra.counter, 1u);
-            last = (t == gridDim.x - 1);
+            if (blockIdx.x != gridDim.x - 1) {
+                // count this block, its partial ordered before the count; no
+                // waiting for a reply, so the block retires at once
+                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ra.counter) : "memory");
+            } else {
+                // the highest-indexed block is dispatched last: it waits
+                // (bounded) until every other block has counted
+                const unsigned want = gridDim.x - 1;
+                long long n = 0;
+                unsigned got;
+                for (;;) {
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(got) : "l"(ra.counter) : "memory");
+                    if (got >= want || ++n > (1ll << 26)) break;
+                    __nanosleep(32);
+                }
+                last = got >= want ? 1 : 0;
+            }
         }
     }
+    if (blockIdx.x != gridDim.x - 1) return;
     __syncthreads();
-    if (!last) return;
-    __threadfence();
+    if (!last) {  // the other blocks never all counted: report, do not hang
+        if (tid == 0) {
+            ra.st->status = QCD_ETIMEOUT;
+            ra.st->done = 1;
+            *ra.counter = 0u;
+            __threadfence();
+        }
+        return;
+    }
     double s[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) s[k] = 0.0;
