@@ -103,6 +103,29 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
             bx = it->second.bx;
         }
     }
+    if (!is_mrhs(sc) && bx * nrhs > 384) {
+        // more right-hand sides than a block of the generic kernels holds:
+        // launch them in groups (no reduction spans the groups)
+        if (sc.red != R_NONE) {
+            set_error_message("a fused reduction over %d right-hand sides is not supported", nrhs);
+            return QCD_EINVAL;
+        }
+        const int per = 384 / bx;
+        for (int r0 = 0; r0 < nrhs; r0 += per) {
+            StencilCall g = sc;
+            g.nrhs = nrhs - r0 < per ? nrhs - r0 : per;
+            g.force_variant = variant;
+            g.force_bx = bx;
+            HVec *vs[5] = {&g.out, &g.in, &g.y, &g.z, &g.aux};
+            for (HVec *v : vs) {
+                if (v->p) v->p = (char *)v->p + (size_t)r0 * sc.rhs_stride * 16;
+                if (v->norm) v->norm += (size_t)r0 * sc.norm_stride;
+            }
+            const int rc = launch_stencil(c, g);
+            if (rc != QCD_OK) return rc;
+        }
+        return QCD_OK;
+    }
     dim3 block(bx, nrhs);
     dim3 grid(nblocks(c->g.Vh, bx));
     if (!is_mrhs(sc) && sc.red != R_NONE && (int)grid.x > c->partial_blocks) {

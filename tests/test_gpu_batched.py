@@ -36,12 +36,12 @@ def batch():
         p["ctx"].close()
 
 
-def run_batch(probs, tol=1e-10, check=True):
+def run_batch(probs, tol=1e-10, check=True, **kw):
     from paper_1709_08785_gb300 import qcd
 
     xs = [torch.zeros_like(p["bd"]) for p in probs]
     infos = qcd.solve_batched([p["ctx"] for p in probs], [p["bd"] for p in probs], xs, [tol] * len(probs),
-                              check=check, precision_levels=2)
+                              check=check, precision_levels=2, **kw)
     torch.cuda.synchronize()
     return xs, infos
 
@@ -105,3 +105,12 @@ def test_batched_rejects_bad_arguments(batch):
         qcd.solve_batched([p["ctx"]], [p["bd"]], [x], [1e-10], precision_levels=3)
     with pytest.raises(qcd.QCDError):  # one context twice
         qcd.solve_batched([p["ctx"], p["ctx"]], [p["bd"], p["bd"]], [x, torch.zeros_like(x)], [1e-10, 1e-10])
+
+
+def test_batched_fp64_outer_level(batch):
+    """The batch with its outer level in FP64 (outer_df64 = 0) instead of DF64."""
+    xs, infos = run_batch(batch, outer_df64=0)
+    for p, x, inf in zip(batch, xs, infos):
+        assert inf["status"] == 0
+        F = oracle.clover_field(p["dims"], p["U"], p["kappa"], 1.0)
+        assert oracle.true_residual(p["dims"], -1, p["U"], F, p["kappa"], p["b"], x.cpu().numpy()) <= 1e-10

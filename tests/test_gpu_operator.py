@@ -115,7 +115,7 @@ def test_dirac_full(lat):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2, 3])
-@pytest.mark.parametrize("nrhs", [3, 12])
+@pytest.mark.parametrize("nrhs", [3, 12, 16])
 def test_multi_rhs_matches_single(lat, prec, nrhs):
     """Each column of a multi-RHS launch equals the single-RHS result (bit
     for bit: same kernel arithmetic) and the oracle."""

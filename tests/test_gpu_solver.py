@@ -180,3 +180,23 @@ def test_solve_repeatable_bitwise(lat8):
     x2, i2 = solve(lat8, precision_levels=2)
     assert np.array_equal(x1, x2)
     assert i1["inner_iters"] == i2["inner_iters"]
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_periodic_time_boundary(levels):
+    """Periodic time (t_bc = +1) on a lattice with ragged 32-site blocks."""
+    from paper_1709_08785_gb300 import qcd
+
+    dims, kappa, csw, t_bc = (6, 2, 4, 10), 0.12, 1.3, 1
+    U = inputs.random_gauge(dims, 0.3, 21)
+    b = inputs.gaussian_source(dims, 22)
+    F = oracle.clover_field(dims, U, kappa, csw)
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    info = ctx.solve(bd, x, tol=1e-12, precision_levels=levels)
+    assert info["status"] == 0
+    assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
+    ctx.close()
