@@ -200,3 +200,42 @@ def test_periodic_time_boundary(levels):
     assert info["status"] == 0
     assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
     ctx.close()
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_degenerate_kappa_zero(levels):
+    """kappa = 0: no hopping and no clover term, D = 1, so x = b exactly."""
+    from paper_1709_08785_gb300 import qcd
+
+    dims = (4, 4, 4, 4)
+    U = inputs.random_gauge(dims, 0.3, 23)
+    b = inputs.gaussian_source(dims, 24)
+    ctx = qcd.Context(dims, -1)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(0.0, 1.0)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    info = ctx.solve(bd, x, tol=1e-12, precision_levels=levels)
+    assert info["status"] == 0 and info["true_resid"] <= 1e-12
+    assert np.max(np.abs(x.cpu().numpy() - b)) <= 1e-13 * np.max(np.abs(b))
+    ctx.close()
+
+
+def test_wilson_without_clover():
+    """csw = 0: the plain Wilson operator (F = 1)."""
+    from paper_1709_08785_gb300 import qcd
+
+    dims, kappa, t_bc = (4, 4, 4, 8), 0.12, -1
+    U = inputs.random_gauge(dims, 0.3, 25)
+    b = inputs.gaussian_source(dims, 26)
+    F = oracle.clover_field(dims, U, kappa, 0.0)
+    assert np.max(np.abs(F - np.eye(12)[None])) == 0.0
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, 0.0)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    info = ctx.solve(bd, x, tol=1e-12, precision_levels=2)
+    assert info["status"] == 0
+    assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
+    ctx.close()
