@@ -19,7 +19,10 @@ __device__ __forceinline__ bool finite_d(double x) { return isfinite(x); }
 
 // The scalar recurrences of BiCGStab (Alg. 2, with alpha = rho0/<r~|q> and
 // beta = (rho1/rho0)(alpha/omega), the standard reading of the printed
-// formulas), run by one thread.
+// formulas), run by one thread at the end of a grid reduction, on the
+// critical path between two kernels: each quotient takes one FP64 division
+// (a long dependent sequence on GB300, whose FP64 rate is 1/64 of FP32) and
+// the breakdown test compares squares instead of taking square roots.
 __device__ inline void finalize(int op, SolverState *st)
 {
     const double *s = st->sum;
@@ -33,8 +36,9 @@ __device__ inline void finalize(int op, SolverState *st)
             st->status = finite_d(den) ? QCD_EBREAKDOWN : QCD_ENONFINITE;
             break;
         }
-        st->alpha[0] = (st->rho0[0] * dr + st->rho0[1] * di) / den;
-        st->alpha[1] = (st->rho0[1] * dr - st->rho0[0] * di) / den;
+        const double inv = 1.0 / den;
+        st->alpha[0] = (st->rho0[0] * dr + st->rho0[1] * di) * inv;
+        st->alpha[1] = (st->rho0[1] * dr - st->rho0[0] * di) * inv;
         break;
     }
     case FIN_S:
@@ -56,8 +60,9 @@ __device__ inline void finalize(int op, SolverState *st)
             st->exit_half = 1;
             break;
         }
-        st->omega[0] = s[0] / tt;
-        st->omega[1] = s[1] / tt;
+        const double inv = 1.0 / tt;
+        st->omega[0] = s[0] * inv;
+        st->omega[1] = s[1] * inv;
         if (st->omega[0] == 0.0 && st->omega[1] == 0.0) {
             st->done = 1;
             st->status = QCD_EBREAKDOWN;
@@ -75,22 +80,21 @@ __device__ inline void finalize(int op, SolverState *st)
         } else if (rr < st->tol2) {
             st->done = 1;
             st->status = QCD_OK;
-        } else if (sqrt(r1r * r1r + r1i * r1i) <= st->bd_eps * sqrt(st->rt2 * rr)) {
+        } else if (st->bd_eps >= 0.0 && r1r * r1r + r1i * r1i <= st->bd_eps * st->bd_eps * (st->rt2 * rr)) {
             st->done = 1;
             st->status = QCD_EBREAKDOWN;
         } else if (st->iter >= st->maxit) {
             st->done = 1;
             st->status = QCD_ENOTCONV;
         } else {
-            // beta = (rho1/rho0) * (alpha/omega)
-            const double d0 = st->rho0[0] * st->rho0[0] + st->rho0[1] * st->rho0[1];
-            const double qr = (r1r * st->rho0[0] + r1i * st->rho0[1]) / d0;
-            const double qi = (r1i * st->rho0[0] - r1r * st->rho0[1]) / d0;
-            const double d1 = st->omega[0] * st->omega[0] + st->omega[1] * st->omega[1];
-            const double ar = (st->alpha[0] * st->omega[0] + st->alpha[1] * st->omega[1]) / d1;
-            const double ai = (st->alpha[1] * st->omega[0] - st->alpha[0] * st->omega[1]) / d1;
-            st->beta[0] = qr * ar - qi * ai;
-            st->beta[1] = qr * ai + qi * ar;
+            // beta = (rho1/rho0) * (alpha/omega) = (rho1 alpha) / (rho0 omega)
+            const double nr = r1r * st->alpha[0] - r1i * st->alpha[1];
+            const double ni = r1r * st->alpha[1] + r1i * st->alpha[0];
+            const double dr = st->rho0[0] * st->omega[0] - st->rho0[1] * st->omega[1];
+            const double di = st->rho0[0] * st->omega[1] + st->rho0[1] * st->omega[0];
+            const double inv = 1.0 / (dr * dr + di * di);
+            st->beta[0] = (nr * dr + ni * di) * inv;
+            st->beta[1] = (ni * dr - nr * di) * inv;
             st->rho0[0] = r1r;
             st->rho0[1] = r1i;
         }
@@ -195,24 +199,22 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
     double s[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) s[k] = 0.0;
-    // eight independent loads in flight per thread: the partials are read in
-    // a few L2 round trips instead of one per grid-stride step
+    // eight independent loads in flight per thread, the last batch
+    // predicated: the partials arrive in ceil(G / 8 nthr) L2 round trips
     const int G = (int)gridDim.x;
-    int b = tid;
-    for (; b + 7 * nthr < G; b += 8 * nthr) {
+    for (int b0 = tid; b0 < G; b0 += 8 * nthr) {
         double t[8][N];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + u * nthr;
 #pragma unroll
-            for (int k = 0; k < N; ++k) t[u][k] = __ldcg(ra.partials + (size_t)(b + u * nthr) * 4 + k);
+            for (int k = 0; k < N; ++k) t[u][k] = b < G ? __ldcg(ra.partials + (size_t)b * 4 + k) : 0.0;
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
             for (int k = 0; k < N; ++k) s[k] += t[u][k];
     }
-    for (; b < G; b += nthr)
-#pragma unroll
-        for (int k = 0; k < N; ++k) s[k] += __ldcg(ra.partials + (size_t)b * 4 + k);
 #pragma unroll
     for (int k = 0; k < N; ++k)
 #pragma unroll
@@ -230,8 +232,9 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
         }
         for (int k = N; k < 4; ++k) ra.st->sum[k] = 0.0;
         finalize(ra.op, ra.st);
+        // no fence: the kernel ends here, and its completion publishes the
+        // state and the counter to the next kernel in stream order
         *ra.counter = 0u;
-        __threadfence();
     }
 }
 
