@@ -660,15 +660,15 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         qcd_ctx *c = ctxs[i];
         cudaStream_t keep = c->stream;
         c->stream = user;
-        // x_o = F_oo^-1 (b_o + kappa H_oe x_e) in the outer precision, then
-        // x rounded to FP64 for the FP64 true residual
-        HVec be, bo, xo, re, ro, X, XO, xoO, boO;
+        // x_o = F_oo^-1 (b_o + kappa H_oe x_e) and the true residual
+        // ||b - D x|| in the outer precision (FP64 or DF64, as in the single
+        // solve), then x rounded to FP64
+        HVec xo, X, XO, xoO, beO, boO, reO, roO;
         int r = QCD_OK;
-        if ((r = get_work(c, QCD_F64, S64_BE, &be)) || (r = get_work(c, QCD_F64, S64_BO, &bo)) ||
-            (r = get_work(c, QCD_F64, S64_XO, &xo)) || (r = get_work(c, QCD_F64, S64_RE, &re)) ||
-            (r = get_work(c, QCD_F64, S64_RO, &ro)) || (r = get_work(c, QCD_F64, S64_LEVEL, &X)) ||
+        if ((r = get_work(c, QCD_F64, S64_XO, &xo)) || (r = get_work(c, QCD_F64, S64_LEVEL, &X)) ||
             (r = get_work(c, PO, S64_LEVEL, &XO)) || (r = get_work(c, PO, S64_XO, &xoO)) ||
-            (r = get_work(c, PO, S64_BO, &boO))) {
+            (r = get_work(c, PO, S64_BE, &beO)) || (r = get_work(c, PO, S64_BO, &boO)) ||
+            (r = get_work(c, PO, S64_RE, &reO)) || (r = get_work(c, PO, S64_RO, &roO))) {
             c->stream = keep;
             return r;
         }
@@ -682,24 +682,24 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         sx.a = 1.0;
         sx.cc = c->kappa;
         r = launch_stencil(c, sx);
-        if (!r && PO != QCD_F64) r = convert_half(c, XO, X);
-        if (!r && PO != QCD_F64) r = convert_half(c, xoO, xo);
         for (int par = 0; par < 2 && !r; ++par) {
             StencilCall sr;
-            sr.prec = QCD_F64;
+            sr.prec = PO;
             sr.mode = M_FULL;
             sr.out_par = par;
-            sr.out = par ? ro : re;
-            sr.in = par ? X : xo;
-            sr.y = par ? xo : X;
+            sr.out = par ? roO : reO;
+            sr.in = par ? XO : xoO;
+            sr.y = par ? xoO : XO;
             sr.a = -1.0;
             sr.cc = c->kappa;
-            sr.z = par ? bo : be;
+            sr.z = par ? boO : beO;
             sr.d = 1.0;
             sr.red = R_NORM;
             sr.red_args = RedArgs{c->partials, c->counters, c->states + ST_AUX, par ? FIN_ADDN + 2 : FIN_SETN + 2};
             r = launch_stencil(c, sr);
         }
+        if (!r && PO != QCD_F64) r = convert_half(c, XO, X);
+        if (!r && PO != QCD_F64) r = convert_half(c, xoO, xo);
         if (!r) r = half_to_canon(c, QCD_F64, 0, X, x[i], 0, 1, 0);
         if (!r) r = half_to_canon(c, QCD_F64, 0, xo, x[i], 1, 1, 0);
         SolverState ha;

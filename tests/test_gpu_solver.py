@@ -85,6 +85,9 @@ def test_even_odd_solves_8c16(lat8, levels):
     assert info["status"] == 0, info
     r = true_res(lat8, x)
     assert r <= 1e-12, (r, info)
+    # the solver's own true residual (DF64 for the nested schemes, whose
+    # rounding of b - D x is ~1e-14 |b|) against the oracle's FP64 one
+    assert abs(info["true_resid"] - r) <= 3e-14, (info["true_resid"], r)
     if levels >= 2:
         assert info["dhat_applies"][1] > 0 and info["outer_iters"] >= 1
     if levels == 3:
@@ -96,7 +99,9 @@ def test_fp64_outer_arithmetic(lat8, levels):
     """The nested schemes with the outer level in FP64 instead of DF64."""
     x, info = solve(lat8, precision_levels=levels, outer_df64=0)
     assert info["status"] == 0, info
-    assert true_res(lat8, x) <= 1e-12
+    r = true_res(lat8, x)
+    assert r <= 1e-12
+    assert abs(info["true_resid"] - r) <= 1e-15, (info["true_resid"], r)
 
 
 def test_host_buffers(lat4):
