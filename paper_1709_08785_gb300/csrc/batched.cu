@@ -444,8 +444,8 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
 {
     qcd_ctx *c0 = ctxs[0];
     cudaStream_t user = c0->stream;
-    // the outer level in DF64 (float pairs) unless FP64 is asked for, as in
-    // the single solve; the true residual is FP64 either way
+    // the outer level and the true residual in DF64 (float pairs) unless
+    // FP64 is asked for, as in the single solve
     const int PO = o.outer_df64 ? QCD_DF64 : QCD_F64;
     void (*kin)(BatchArgs) = o.outer_df64 ? batched_inner<CDF> : batched_inner<C64>;
     void (*kout)(BatchArgs) = o.outer_df64 ? batched_outer<CDF> : batched_outer<C64>;
