@@ -317,8 +317,6 @@ struct ApiBufs {
 
 int api_bufs(qcd_ctx *c, int prec, int nrhs, ApiBufs *b)
 {
-    static thread_local int dummy = 0;
-    (void)dummy;
     const size_t hb = hvec_bytes(c->g, prec);
     const size_t nb = prec == QCD_F16 ? (size_t)c->g.Vh_pad * sizeof(float) : 0;
     // three regions of nrhs vectors each, plus norms
