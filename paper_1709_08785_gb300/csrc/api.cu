@@ -243,6 +243,12 @@ extern "C" int qcd_destroy(qcd_ctx *c)
         cudaEventDestroy(p.b);
     }
     for (auto e : c->event_pool) cudaEventDestroy(e);
+    if (c->out_stream) {
+        cudaStreamSynchronize(c->out_stream);
+        cudaStreamDestroy(c->out_stream);
+    }
+    if (c->out_ready) cudaEventDestroy(c->out_ready);
+    if (c->out_copied) cudaEventDestroy(c->out_copied);
     delete c;
     return QCD_OK;
 }
@@ -522,10 +528,28 @@ extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const q
             if (o.use_x0) QCD_CUDA_CHECK(cudaMemcpyAsync(xd, x, vbytes, cudaMemcpyHostToDevice, c->stream));
         }
     }
+    if (!x_dev) {
+        // the solver copies x out as soon as it is emitted (before its true
+        // residual is checked) on a second stream
+        if (!c->out_stream) {
+            QCD_CUDA_CHECK(cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking));
+            QCD_CUDA_CHECK(cudaEventCreateWithFlags(&c->out_ready, cudaEventDisableTiming));
+            QCD_CUDA_CHECK(cudaEventCreateWithFlags(&c->out_copied, cudaEventDisableTiming));
+        }
+        c->x_host = x;
+        c->x_host_bytes = vbytes;
+        c->x_host_issued = false;
+    }
     int rc = solve(c, bd, xd, tol, o, info);
     if (!x_dev) {
-        QCD_CUDA_CHECK(cudaMemcpyAsync(x, xd, vbytes, cudaMemcpyDeviceToHost, c->stream));
+        const bool issued = c->x_host_issued;
+        c->x_host = nullptr;
+        c->x_host_issued = false;
+        // a path that emitted no x (the unpreconditioned solver, an early
+        // error) is copied out here, after the solve
+        if (!issued) QCD_CUDA_CHECK(cudaMemcpyAsync(x, xd, vbytes, cudaMemcpyDeviceToHost, c->stream));
         QCD_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        QCD_CUDA_CHECK(cudaStreamSynchronize(c->out_stream));
     }
     return rc;
 }

@@ -122,6 +122,15 @@ struct qcd_ctx {
     void *staging = nullptr;        // canonical full-lattice complex128 staging
     size_t staging_bytes = 0;
 
+    // host output of qcd_solve: when x_host is set, the even-odd solver
+    // copies each FP64 solution it emits to x_host on out_stream, so that
+    // the copy overlaps the true-residual check
+    void *x_host = nullptr;
+    size_t x_host_bytes = 0;
+    bool x_host_issued = false;  // a copy of the current x is in flight or done
+    cudaStream_t out_stream = nullptr;
+    cudaEvent_t out_ready = nullptr, out_copied = nullptr;
+
     // profiling
     bool profiling = false;
     struct Pending {

@@ -264,6 +264,25 @@ int true_residual(Solver &S, int P, HVec xe, HVec xo, HVec be, HVec bo)
     return QCD_OK;
 }
 
+// x (canonical FP64, device) from the half vectors; when the caller's x is
+// in host memory, its copy is issued on the output stream at once, so that
+// it overlaps the true-residual check that follows.  A later emission (after
+// a restart) first waits for that copy to finish.
+int emit_x(qcd_ctx *c, HVec xe, HVec xo, void *x)
+{
+    if (c->x_host && c->x_host_issued) QCD_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->out_copied, 0));
+    TRY(half_to_canon(c, QCD_F64, 0, xe, x, 0, 1, 0));
+    TRY(half_to_canon(c, QCD_F64, 0, xo, x, 1, 1, 0));
+    if (c->x_host) {
+        QCD_CUDA_CHECK(cudaEventRecord(c->out_ready, c->stream));
+        QCD_CUDA_CHECK(cudaStreamWaitEvent(c->out_stream, c->out_ready, 0));
+        QCD_CUDA_CHECK(cudaMemcpyAsync(c->x_host, x, c->x_host_bytes, cudaMemcpyDeviceToHost, c->out_stream));
+        QCD_CUDA_CHECK(cudaEventRecord(c->out_copied, c->out_stream));
+        c->x_host_issued = true;
+    }
+    return QCD_OK;
+}
+
 int solve_eo(Solver &S, const void *b, void *x, double tol)
 {
     qcd_ctx *c = S.c;
@@ -354,11 +373,12 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         s.a = 1.0;
         s.cc = c->kappa;
         TRY(launch_stencil(c, s));
-        TRY(true_residual(S, P0, O.x, xoP, beP, boP));
         if (P0 != QCD_F64) {
             TRY(convert_half(c, O.x, xe64));
             TRY(convert_half(c, xoP, S.xo));
         }
+        TRY(emit_x(c, xe64, S.xo, x));
+        TRY(true_residual(S, P0, O.x, xoP, beP, boP));
         TRY(read_state(c, ST_AUX, &ha));
         S.info.true_resid = resid_ratio(ha);
         if (!std::isfinite(S.info.true_resid)) {
@@ -381,8 +401,6 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         TRY(residual_eo(S, O.x, O.r, O.st, FIN_NONE));
         TRY(blas_init(c, P0, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_RESTART));
     }
-    TRY(half_to_canon(c, QCD_F64, 0, xe64, x, 0, 1, 0));
-    TRY(half_to_canon(c, QCD_F64, 0, S.xo, x, 1, 1, 0));
     return status;
 }
 

@@ -154,6 +154,23 @@ def test_singular_clover_block_reported(lat4):
     ctx.close()
 
 
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_pinned_host_buffers_match_device(lat8, levels):
+    """Pinned host b and x: the solution is copied out while the true
+    residual is checked, and equals the device-buffer solve bit for bit (the
+    reductions are deterministic)."""
+    bd = torch.from_numpy(lat8["b"]).cuda()
+    xd = torch.zeros_like(bd)
+    info_d = lat8["ctx"].solve(bd, xd, tol=1e-12, precision_levels=levels)
+    bh = torch.from_numpy(lat8["b"]).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    info_h = lat8["ctx"].solve(bh, xh, tol=1e-12, precision_levels=levels)
+    assert info_d["status"] == 0 and info_h["status"] == 0
+    assert torch.equal(xh, xd.cpu())
+    assert info_h["true_resid"] == info_d["true_resid"]
+    assert true_res(lat8, xh.numpy()) <= 1e-12
+
+
 def test_iteration_cap(lat4):
     bd = torch.from_numpy(lat4["b"]).cuda()
     x = torch.zeros_like(bd)
