@@ -190,7 +190,9 @@ void qcd_solve_opts_default(qcd_solve_opts *opts);
 /* Solve D x = b to ||b - D x|| / ||b|| <= tol (recomputed at exit;
  * a restart from the true residual follows if the recursive residual
  * drifted).  b, x: full-lattice complex128 [V][4][3], device or host memory
- * (host buffers are staged through the device inside the call).  The
+ * (host buffers are staged through the device inside the call; a host x
+ * is copied out on a second stream of the context while the true residual
+ * is checked, and is complete when the call returns).  The
  * nested scheme is Alg. 1 (flexible BiCGStab, FP64) around Alg. 2
  * (BiCGStab on a unit-norm right-hand side from x = 0, lower precision).
  * Blocks until the solve ends.  info may be NULL.
