@@ -5,7 +5,7 @@ BiCGStab, with the clover Dslash (MULT) bandwidth against the HBM roofline.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one complete qcd_solve (b^_e preparation, the nested iteration,
-x_o reconstruction and the true-residual check) from a device-resident
+x_o reconstruction and the FP64 true-residual check) from a device-resident
 source; every step must reach ||b - D x|| / ||b|| <= 1e-12.  Under torchrun
 (N > 1) every rank solves its own replica (no collective on the data path);
 the time is the maximum over ranks.  Prints one JSON line on rank 0.

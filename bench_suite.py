@@ -15,8 +15,7 @@
                           protocol (2000 or 4000 D^) on L^3 x 2L, SOLVE rate by Table I counts
 
 Inputs are the seeded synthetic fields of paper_1709_08785_gb300.inputs; every
-solve's true residual is computed by the library (in the outer level's precision,
-DF64 or FP64) and checked here.
+solve's true residual is computed in FP64 by the library and checked here.
 """
 import argparse
 import json

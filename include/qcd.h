@@ -162,12 +162,11 @@ typedef struct {
                              unit-norm right-hand side (Alg. 2); level 2, 3 */
     int max_outer;        /* iteration cap of the FP64 level */
     int max_inner[2];     /* iteration caps of the lower levels */
-    int max_restarts;     /* restarts from the true residual */
+    int max_restarts;     /* restarts from the true residual (FP64) */
     int use_x0;           /* 1: x holds an initial guess; 0: x = 0 (Alg. 1) */
     int outer_df64;       /* precision_levels >= 2: 1 (default) computes the
-                             outer level and the true residual in QCD_DF64
-                             (its rounding of b - D x ~1e-14 ||b||), 0 both
-                             in FP64 */
+                             outer level in QCD_DF64, 0 in FP64; the final
+                             true residual is FP64 either way */
 } qcd_solve_opts;
 
 typedef struct {
@@ -176,9 +175,7 @@ typedef struct {
     int inner_iters[2];    /* iterations summed over the lower levels */
     int restarts;          /* true-residual restarts */
     long dhat_applies[3];  /* D^ (or D) applications by precision F64/F32/F16 */
-    double true_resid;     /* ||b - D x|| / ||b|| at exit, computed in the
-                              outer level's precision (FP64 or DF64) with
-                              FP64 accumulation */
+    double true_resid;     /* ||b - D x|| / ||b|| in FP64 at exit */
     double seconds;        /* wall time of the call (device events) */
 } qcd_solve_info;
 
@@ -187,7 +184,7 @@ typedef struct {
  * outer_df64 1. */
 void qcd_solve_opts_default(qcd_solve_opts *opts);
 
-/* Solve D x = b to ||b - D x|| / ||b|| <= tol (recomputed at exit;
+/* Solve D x = b to ||b - D x|| / ||b|| <= tol (recomputed in FP64 at exit;
  * a restart from the true residual follows if the recursive residual
  * drifted).  b, x: full-lattice complex128 [V][4][3], device or host memory
  * (host buffers are staged through the device inside the call; a host x

@@ -444,8 +444,8 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
 {
     qcd_ctx *c0 = ctxs[0];
     cudaStream_t user = c0->stream;
-    // the outer level and the true residual in DF64 (float pairs) unless
-    // FP64 is asked for, as in the single solve
+    // the outer level in DF64 (float pairs) unless FP64 is asked for, as in
+    // the single solve; the true residual is FP64 either way
     const int PO = o.outer_df64 ? QCD_DF64 : QCD_F64;
     void (*kin)(BatchArgs) = o.outer_df64 ? batched_inner<CDF> : batched_inner<C64>;
     void (*kout)(BatchArgs) = o.outer_df64 ? batched_outer<CDF> : batched_outer<C64>;
@@ -660,15 +660,15 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         qcd_ctx *c = ctxs[i];
         cudaStream_t keep = c->stream;
         c->stream = user;
-        // x_o = F_oo^-1 (b_o + kappa H_oe x_e) and the true residual
-        // ||b - D x|| in the outer precision (FP64 or DF64, as in the single
-        // solve), then x rounded to FP64
-        HVec xo, X, XO, xoO, beO, boO, reO, roO;
+        // x_o = F_oo^-1 (b_o + kappa H_oe x_e) in the outer precision, then
+        // x rounded to FP64 for the FP64 true residual
+        HVec be, bo, xo, re, ro, X, XO, xoO, boO;
         int r = QCD_OK;
-        if ((r = get_work(c, QCD_F64, S64_XO, &xo)) || (r = get_work(c, QCD_F64, S64_LEVEL, &X)) ||
+        if ((r = get_work(c, QCD_F64, S64_BE, &be)) || (r = get_work(c, QCD_F64, S64_BO, &bo)) ||
+            (r = get_work(c, QCD_F64, S64_XO, &xo)) || (r = get_work(c, QCD_F64, S64_RE, &re)) ||
+            (r = get_work(c, QCD_F64, S64_RO, &ro)) || (r = get_work(c, QCD_F64, S64_LEVEL, &X)) ||
             (r = get_work(c, PO, S64_LEVEL, &XO)) || (r = get_work(c, PO, S64_XO, &xoO)) ||
-            (r = get_work(c, PO, S64_BE, &beO)) || (r = get_work(c, PO, S64_BO, &boO)) ||
-            (r = get_work(c, PO, S64_RE, &reO)) || (r = get_work(c, PO, S64_RO, &roO))) {
+            (r = get_work(c, PO, S64_BO, &boO))) {
             c->stream = keep;
             return r;
         }
@@ -682,24 +682,24 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         sx.a = 1.0;
         sx.cc = c->kappa;
         r = launch_stencil(c, sx);
+        if (!r && PO != QCD_F64) r = convert_half(c, XO, X);
+        if (!r && PO != QCD_F64) r = convert_half(c, xoO, xo);
         for (int par = 0; par < 2 && !r; ++par) {
             StencilCall sr;
-            sr.prec = PO;
+            sr.prec = QCD_F64;
             sr.mode = M_FULL;
             sr.out_par = par;
-            sr.out = par ? roO : reO;
-            sr.in = par ? XO : xoO;
-            sr.y = par ? xoO : XO;
+            sr.out = par ? ro : re;
+            sr.in = par ? X : xo;
+            sr.y = par ? xo : X;
             sr.a = -1.0;
             sr.cc = c->kappa;
-            sr.z = par ? boO : beO;
+            sr.z = par ? bo : be;
             sr.d = 1.0;
             sr.red = R_NORM;
             sr.red_args = RedArgs{c->partials, c->counters, c->states + ST_AUX, par ? FIN_ADDN + 2 : FIN_SETN + 2};
             r = launch_stencil(c, sr);
         }
-        if (!r && PO != QCD_F64) r = convert_half(c, XO, X);
-        if (!r && PO != QCD_F64) r = convert_half(c, xoO, xo);
         if (!r) r = half_to_canon(c, QCD_F64, 0, X, x[i], 0, 1, 0);
         if (!r) r = half_to_canon(c, QCD_F64, 0, xo, x[i], 1, 1, 0);
         SolverState ha;

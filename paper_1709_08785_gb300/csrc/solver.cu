@@ -291,15 +291,14 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     // The outer level computes in P0: FP64 for the plain BiCGStab, and for
     // the nested schemes by default DF64 (float pairs, ~48 bits; GB300's
     // FP64 rate is ~1/64 of its FP32 rate).  The true-residual check
-    // ||b - D x|| of the full solution runs in P0 as well: in DF64 its
-    // rounding, ~1e-14 |b|, stays two orders below the 1e-12 tolerances, and
-    // it takes ~0.6 ms at 24^3x48 against ~1.6 ms in FP64.
+    // ||b - D x|| that decides convergence is FP64 either way, from the FP64
+    // links and clover term and x rounded to FP64.
     const int P0 = (S.o.precision_levels >= 2 && S.o.outer_df64) ? QCD_DF64 : QCD_F64;
     TRY(get_work(c, QCD_F64, 0, &S.be));
     TRY(get_work(c, QCD_F64, 1, &S.bo));
     TRY(get_work(c, QCD_F64, 3, &S.xo));
-    TRY(get_work(c, P0, 4, &S.re));
-    TRY(get_work(c, P0, 5, &S.ro));
+    TRY(get_work(c, QCD_F64, 4, &S.re));
+    TRY(get_work(c, QCD_F64, 5, &S.ro));
     TRY(get_work(c, P0, 2, &S.bhat));
     TRY(get_level(c, O, P0, 6, ST_OUTER));
     HVec beP = S.be, boP = S.bo, xoP = S.xo, xe64 = O.x;
@@ -378,7 +377,7 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
             TRY(convert_half(c, xoP, S.xo));
         }
         TRY(emit_x(c, xe64, S.xo, x));
-        TRY(true_residual(S, P0, O.x, xoP, beP, boP));
+        TRY(true_residual(S, QCD_F64, xe64, S.xo, S.be, S.bo));
         TRY(read_state(c, ST_AUX, &ha));
         S.info.true_resid = resid_ratio(ha);
         if (!std::isfinite(S.info.true_resid)) {
