@@ -220,6 +220,18 @@ FLOP_DHAT, FLOP_AXPY, FLOP_DOT, FLOP_NORM = 4512, 96, 96, 48
 FLOP_INNER_ITER = 2 * FLOP_DHAT + 6 * FLOP_AXPY + 3 * FLOP_DOT + 3 * FLOP_NORM  # 10032
 
 
+def fixed_work_solve(ctx, b, x, n_dhat):
+    """One solve of the fixed-work protocol: n_dhat inner D^ as n_dhat/500
+    preconditioner calls of 250 FP32 iterations each (the inner tolerance is
+    never reached), two per outer iteration, each followed by one outer D^;
+    no restart.  Returns the solve's info (status QCD_ENOTCONV: tol 1e-30)."""
+    from paper_1709_08785_gb300 import qcd
+
+    opts = qcd.default_opts(precision_levels=2, inner_tol=[1e-30, 1e-2], max_inner=[250, 250],
+                            max_outer=n_dhat // 1000, max_restarts=0)
+    return ctx.solve(b, x, tol=1e-30, opts=opts, check=False)
+
+
 def w_fixed_work(args):
     """The paper's fixed-work protocol (Sec. IV): 2000 (or 4000) D^ in the
     nested solver, as 4 (or 8) sets of 500 inner D^ (250 FP32 iterations, no
@@ -243,17 +255,13 @@ def w_fixed_work(args):
     del U
     ctx.autotune(TUNE_CACHE)
     x = torch.zeros_like(b)
-    # the inner tolerance is never reached: every preconditioner call runs
-    # its 250 iterations (500 D^); each outer iteration calls it twice
     n_outer = args.dhat // 1000
-    opts = qcd.default_opts(precision_levels=2, inner_tol=[1e-30, 1e-2], max_inner=[250, 250], max_outer=n_outer,
-                            max_restarts=0)
-    ctx.solve(b, x, tol=1e-30, opts=opts, check=False)  # warm-up
+    fixed_work_solve(ctx, b, x, args.dhat)  # warm-up
     ts = []
     for _ in range(2):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        info = ctx.solve(b, x, tol=1e-30, opts=opts, check=False)
+        info = fixed_work_solve(ctx, b, x, args.dhat)
         e1.record()
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1) * 1e-3)

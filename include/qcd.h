@@ -122,8 +122,10 @@ int qcd_dslash_eo(qcd_ctx *ctx, void *out, const void *in, int out_parity, int d
  * cudaFree or other allocating routine.  The context (qcd_create,
  * qcd_gauge_load) is still set up beforehand by the caller.
  * Limits: nrhs = 1; the input and output of one half vector must fit in
- * 24 MiB: Vh <= 65536 sites in QCD_F64 (a 16^3 x 32 lattice), more in the
- * lower precisions; larger lattices return QCD_EINVAL.
+ * 24 MiB: Vh <= 65536 sites in QCD_F64 or QCD_DF64 (a 16^3 x 32 lattice),
+ * more in the lower precisions; larger lattices return QCD_EINVAL.  The
+ * context's device must be the current device (QCD_EINVAL otherwise): the
+ * array has one address per device.
  * The first call on each device looks up the array's device address (with
  * that device current), and the first call with each precision and dagger
  * value lets the driver load the kernels it uses (with lazy module loading
@@ -164,9 +166,18 @@ typedef struct {
     int max_inner[2];     /* iteration caps of the lower levels */
     int max_restarts;     /* restarts from the true residual (FP64) */
     int use_x0;           /* 1: x holds an initial guess; 0: x = 0 (Alg. 1) */
-    int outer_df64;       /* precision_levels >= 2: 1 (default) computes the
-                             outer level in QCD_DF64, 0 in FP64; the final
-                             true residual is FP64 either way */
+    int outer_df64;       /* arithmetic of the outer level (Alg. 1) when
+                             precision_levels >= 2:
+                             0: FP64 throughout;
+                             1 (default): the solution x_e, the source b^_e
+                                (Eq. 6) and the reconstruction x_o (Eq. 7)
+                                are FP64 and accumulated in FP64 arithmetic;
+                                the outer D^ applications and the iteration's
+                                own vectors (r, r~, p, q, t, v) are QCD_DF64;
+                             2: QCD_DF64 for all of the outer level.
+                             Outer dot products and norms are summed in FP64
+                             and the final true residual is FP64 in every
+                             mode; QCD_EINVAL outside 0..2 */
 } qcd_solve_opts;
 
 typedef struct {
@@ -255,11 +266,12 @@ typedef enum {
     QCD_K_MULT_F64 = 0,  /* stencil kernels (MULT, D^, b^, x_o, D), by precision; */
     QCD_K_MULT_F32 = 1,  /* FP32: all but the second half of D^, which is QCD_K_DHAT_F32 */
     QCD_K_MULT_F16 = 2,
-    QCD_K_BLAS = 3,      /* fused BLAS-1 + reduction kernels */
+    QCD_K_BLAS = 3,      /* fused BLAS-1 + reduction kernels (all but the FP32 level's) */
     QCD_K_OTHER = 4,
     QCD_K_DHAT_F32 = 5,  /* FP32 second half of D^ with its fused update and dot products */
     QCD_K_MULT_DF64 = 6, /* DF64 stencil kernels */
-    QCD_K_COUNT = 7
+    QCD_K_BLAS_F32 = 7,  /* fused BLAS-1 + reduction kernels of the FP32 level */
+    QCD_K_COUNT = 8
 } qcd_kernel_class;
 
 typedef struct {

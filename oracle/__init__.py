@@ -19,27 +19,50 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qcd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_lib = None
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+_libs = {}
+_openmp = False
+
+
+def _compile(so: str, extra, force: bool):
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + ".tmp%d" % os.getpid()
+        # no FMA contraction (the ISO C mode's default, stated): every host
+        # rounds each operation the same way
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared"] + list(extra) +
+                              ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, so)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/_build/liboracle.so."""
+    """Compile the oracle with gcc into oracle/_build/liboracle.so, and the
+    same source with OpenMP (site loops split across threads, nothing else
+    changed) into liboracle_omp.so for multi-core timings."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(
-            ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        )
-        os.replace(tmp, _SO)
+    _compile(_SO, [], force)
+    _compile(_SO_OMP, ["-fopenmp"], force)
     return _SO
 
 
+def use_openmp(on: bool, threads: int | None = None) -> int:
+    """Route every later oracle call to the OpenMP build (on) or the
+    single-threaded one; returns the threads the site loops then use."""
+    global _openmp
+    _openmp = bool(on)
+    L = lib()
+    if on and threads:
+        L.oracle_set_threads(int(threads))
+    return int(L.oracle_threads())
+
+
 def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
-        _lib.oracle_true_residual.restype = ctypes.c_double
-    return _lib
+    if _openmp not in _libs:
+        build()
+        L = ctypes.CDLL(_SO_OMP if _openmp else _SO)
+        L.oracle_true_residual.restype = ctypes.c_double
+        L.oracle_threads.restype = ctypes.c_int
+        _libs[_openmp] = L
+    return _libs[_openmp]
 
 
 def _dims(dims):

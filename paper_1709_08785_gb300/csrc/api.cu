@@ -504,7 +504,7 @@ extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const q
     if (opts) o = *opts;
     if (o.precision_levels < 1 || o.precision_levels > 3 || (!o.even_odd && o.precision_levels != 1) ||
         !(tol > 0.0) || o.max_outer < 1 || o.max_inner[0] < 1 || o.max_inner[1] < 1 || o.max_restarts < 0 ||
-        !(o.inner_tol[0] > 0.0) || !(o.inner_tol[1] > 0.0)) {
+        !(o.inner_tol[0] > 0.0) || !(o.inner_tol[1] > 0.0) || o.outer_df64 < 0 || o.outer_df64 > 2) {
         set_error_message("invalid solver options");
         return QCD_EINVAL;
     }
@@ -540,6 +540,9 @@ extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const q
         c->x_host_bytes = vbytes;
         c->x_host_issued = false;
     }
+    // the reduction counters start from zero: a bounded wait that gave up
+    // (QCD_ETIMEOUT) in an earlier call may have left a count behind
+    QCD_CUDA_CHECK(cudaMemsetAsync(c->counters, 0, 64 * sizeof(unsigned), c->stream));
     int rc = solve(c, bd, xd, tol, o, info);
     if (!x_dev) {
         const bool issued = c->x_host_issued;
@@ -582,7 +585,7 @@ extern "C" int qcd_solve_batched(qcd_ctx *const *ctxs, int n, const void *const 
     qcd_solve_opts_default(&o);
     if (opts) o = *opts;
     if (o.precision_levels != 2 || !o.even_odd || o.use_x0 || o.max_outer < 1 || o.max_inner[0] < 1 ||
-        !(o.inner_tol[0] > 0.0)) {
+        !(o.inner_tol[0] > 0.0) || o.outer_df64 < 0 || o.outer_df64 > 2) {
         set_error_message("batched solves run the even-odd FP64/FP32 scheme from x = 0");
         return QCD_EINVAL;
     }
@@ -601,6 +604,9 @@ extern "C" int qcd_solve_batched(qcd_ctx *const *ctxs, int n, const void *const 
                 return QCD_EINVAL;
             }
     }
+    // every context's reduction counters from zero (see qcd_solve)
+    for (int i = 0; i < n; ++i)
+        QCD_CUDA_CHECK(cudaMemsetAsync(ctxs[i]->counters, 0, 64 * sizeof(unsigned), ctxs[0]->stream));
     cudaEvent_t e0, e1;
     QCD_CUDA_CHECK(cudaEventCreate(&e0));
     QCD_CUDA_CHECK(cudaEventCreate(&e1));

@@ -6,8 +6,10 @@
 //     init | { MULT | D^ 2nd half + <r~|q> | alpha | s = r - a q, |s| | exit? |
 //              MULT | D^ 2nd half + <t|s>,|t|^2 | omega | x, r, <r~|r> | beta, exit? | p }
 //     | lift v = |src| x into the outer precision
-//   batched_outer (DF64 by default, FP64 on request): outer D^ with its dot |
-//     alpha or omega | outer update and exit test | (second half-step) p update
+//   batched_outer (the outer D^ and recursions in DF64 by default, FP64 on
+//     request; the solution x_e accumulated in FP64 unless the all-DF64
+//     outer level is asked for): outer D^ with its dot | alpha or omega |
+//     outer update and exit test | (second half-step) p update
 //
 // Each phase walks work tiles (256 sites of one parity of one problem)
 // across all lattices; tiles of problems that have finished are skipped.
@@ -50,7 +52,7 @@ struct BProb {
     GaugePtr U32, UO;
     CloverPtr Ci32, CiO;                       // UO, CiO: in the outer level's precision
     SpinorPtr x, r, rt, p, q, t, tmp;          // FP32 inner (tmp: odd parity)
-    SpinorPtr X, R, RT, P, Q, T, Vv, TMP;      // outer level: DF64 (default) or FP64
+    SpinorPtr X, R, RT, P, Q, T, Vv, TMP;      // outer level: DF64 (default) or FP64; X in PX
     SolverState *in, *out;                     // inner, outer scalars
     double *partials;                          // [ntiles][4]
     int tile0, ntiles;
@@ -153,8 +155,9 @@ __device__ __forceinline__ void hop_outer(const BProb &pr, const SpinorPtr &in, 
 }
 
 // one phase over all tiles of all live problems; PO: the outer level's
-// (coherent) precision, DF64 or FP64
-template <int PO, bool OUTER>
+// (coherent) precision, DF64 or FP64; PX: the precision of the outer
+// solution x_e (FP64, or PO)
+template <int PO, int PX, bool OUTER>
 __device__ void run_phase(const BatchArgs &A, int ph)
 {
     using TO = typename Prec<PO>::T;
@@ -279,8 +282,13 @@ __device__ void run_phase(const BatchArgs &A, int ph)
         case PH_OUPD:
             if constexpr (!OUTER) break;
             if (in_range) {
-                if (A.half == 0) OpFlex1<PO>{pr.X, pr.Vv, pr.R, pr.Q, &s_out}(cb, acc);
-                else OpFlex2<PO>{pr.X, pr.Vv, pr.R, pr.T, pr.RT, &s_out}(cb, acc);
+                if constexpr (PX == PO) {
+                    if (A.half == 0) OpFlex1<PO>{pr.X, pr.Vv, pr.R, pr.Q, &s_out}(cb, acc);
+                    else OpFlex2<PO>{pr.X, pr.Vv, pr.R, pr.T, pr.RT, &s_out}(cb, acc);
+                } else {
+                    if (A.half == 0) OpFlex1X<PO, PX>{pr.X, pr.Vv, pr.R, pr.Q, &s_out}(cb, acc);
+                    else OpFlex2X<PO, PX>{pr.X, pr.Vv, pr.R, pr.T, pr.RT, &s_out}(cb, acc);
+                }
             }
             nred = 3;
             break;
@@ -380,30 +388,30 @@ template <int PO>
 __global__ void __launch_bounds__(TILE, 3) batched_inner(BatchArgs A)
 {
     inner_start(A);
-    run_phase<PO, false>(A, PH_INIT);
+    run_phase<PO, PO, false>(A, PH_INIT);
     QCD_SYNC();
     for (int it = 0; it <= A.inner_maxit; ++it) {
-        run_phase<PO, false>(A, PH_MULT_P);
+        run_phase<PO, PO, false>(A, PH_MULT_P);
         QCD_SYNC();
-        run_phase<PO, false>(A, PH_DHAT_Q);
+        run_phase<PO, PO, false>(A, PH_DHAT_Q);
         QCD_SYNC();
         run_finalise(A, PH_DHAT_Q);
         QCD_SYNC();
-        run_phase<PO, false>(A, PH_S);
+        run_phase<PO, PO, false>(A, PH_S);
         QCD_SYNC();
         run_finalise(A, PH_S);
         QCD_SYNC();
-        run_phase<PO, false>(A, PH_MULT_S);
+        run_phase<PO, PO, false>(A, PH_MULT_S);
         QCD_SYNC();
-        run_phase<PO, false>(A, PH_DHAT_T);
+        run_phase<PO, PO, false>(A, PH_DHAT_T);
         QCD_SYNC();
         run_finalise(A, PH_DHAT_T);
         QCD_SYNC();
-        run_phase<PO, false>(A, PH_X);
+        run_phase<PO, PO, false>(A, PH_X);
         QCD_SYNC();
         run_finalise(A, PH_X);
         QCD_SYNC();
-        run_phase<PO, false>(A, PH_P);
+        run_phase<PO, PO, false>(A, PH_P);
         QCD_SYNC();
         bool any = false;
         for (int pi = 0; pi < A.nprob && !any; ++pi)
@@ -411,24 +419,24 @@ __global__ void __launch_bounds__(TILE, 3) batched_inner(BatchArgs A)
         if (!any) break;
     }
     inner_account(A);
-    run_phase<PO, false>(A, PH_LIFT);
+    run_phase<PO, PO, false>(A, PH_LIFT);
 }
 
-template <int PO>
+template <int PO, int PX>
 __global__ void __launch_bounds__(TILE) batched_outer(BatchArgs A)
 {
-    run_phase<PO, true>(A, PH_OMULT);
+    run_phase<PO, PX, true>(A, PH_OMULT);
     QCD_SYNC();
-    run_phase<PO, true>(A, PH_ODHAT);
+    run_phase<PO, PX, true>(A, PH_ODHAT);
     QCD_SYNC();
     run_finalise(A, PH_ODHAT);
     QCD_SYNC();
-    run_phase<PO, true>(A, PH_OUPD);
+    run_phase<PO, PX, true>(A, PH_OUPD);
     QCD_SYNC();
     run_finalise(A, PH_OUPD);
     if (A.half == 1) {
         QCD_SYNC();
-        run_phase<PO, true>(A, PH_OP);
+        run_phase<PO, PX, true>(A, PH_OP);
         QCD_SYNC();
         run_finalise(A, PH_OP);
     }
@@ -444,11 +452,16 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
 {
     qcd_ctx *c0 = ctxs[0];
     cudaStream_t user = c0->stream;
-    // the outer level in DF64 (float pairs) unless FP64 is asked for, as in
-    // the single solve; the true residual is FP64 either way
-    const int PO = o.outer_df64 ? QCD_DF64 : QCD_F64;
-    void (*kin)(BatchArgs) = o.outer_df64 ? batched_inner<CDF> : batched_inner<C64>;
-    void (*kout)(BatchArgs) = o.outer_df64 ? batched_outer<CDF> : batched_outer<C64>;
+    // the outer level's precisions as in the single solve (outer_df64):
+    // PO for the outer D^ and recursions, PX for x_e, b^_e and x_o; the true
+    // residual is FP64 in every mode
+    const int mode = o.outer_df64;
+    const int PO = mode ? QCD_DF64 : QCD_F64;
+    const int PX = mode == 2 ? QCD_DF64 : QCD_F64;
+    void (*kin)(BatchArgs) = mode ? batched_inner<CDF> : batched_inner<C64>;
+    void (*kout)(BatchArgs) = mode == 0   ? batched_outer<C64, C64>
+                              : mode == 1 ? batched_outer<CDF, C64>
+                                          : batched_outer<CDF, CDF>;
     std::vector<BProb> host(n);
     int tiles = 0;
     // ---- per problem: b^_e, |b|^2, and the outer start (same steps as the single solve)
@@ -462,16 +475,20 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
             set_error_message("problem %d: no clover term", i);
             return QCD_ESTATE;
         }
-        // FP64 b_e, b_o (norms, true residual); the outer level in PO
-        HVec be, bo, beO, boO, bh, LO[8], L32[8];
+        // FP64 b_e, b_o (norms, true residual); b^_e and x_e in PX; the
+        // outer iteration's vectors in PO
+        HVec be, bo, beX, boX, bh, bh0, XX, tmpX, LO[8], L32[8];
         int rc;
         if ((rc = get_work(c, QCD_F64, S64_BE, &be)) || (rc = get_work(c, QCD_F64, S64_BO, &bo)) ||
-            (rc = get_work(c, PO, S64_BE, &beO)) || (rc = get_work(c, PO, S64_BO, &boO)) ||
-            (rc = get_work(c, PO, S64_BHAT, &bh)))
+            (rc = get_work(c, PX, S64_BE, &beX)) || (rc = get_work(c, PX, S64_BO, &boX)) ||
+            (rc = get_work(c, PX, S64_BHAT, &bh)) || (rc = get_work(c, PO, S64_BHAT, &bh0)) ||
+            (rc = get_work(c, PX, S64_LEVEL, &XX)))
             return rc;
         for (int k = 0; k < 8; ++k)
             if ((rc = get_work(c, PO, S64_LEVEL + k, &LO[k])) || (rc = get_work(c, QCD_F32, S32_LEVEL + k, &L32[k])))
                 return rc;
+        tmpX = LO[7];
+        if (PX != PO && (rc = get_work(c, QCD_F64, S64_RE, &tmpX))) return rc;
         SolverState *outer = c->states + ST_OUTER, *inner = c->states + ST_MID, *aux = c->states + ST_AUX;
         const int nn = c->g.Vh_pad;
         cudaStream_t keep = c->stream;
@@ -481,24 +498,26 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         if (!rc) rc = state_init(c, aux, 0.0, 0.0, 0, 0.0, 0);
         if (!rc) rc = blas_norm2(c, QCD_F64, nn, be, aux, FIN_SETN + 0);
         if (!rc) rc = blas_norm2(c, QCD_F64, nn, bo, aux, FIN_ADDN + 0);
-        if (!rc && PO != QCD_F64) rc = convert_half(c, be, beO);
-        if (!rc && PO != QCD_F64) rc = convert_half(c, bo, boO);
-        if (!rc) rc = clover_apply_half(c, PO, 1, 1, boO, LO[7], 1, 0);
+        if (!rc && PX != QCD_F64) rc = convert_half(c, be, beX);
+        if (!rc && PX != QCD_F64) rc = convert_half(c, bo, boX);
+        if (!rc) rc = clover_apply_half(c, PX, 1, 1, boX, tmpX, 1, 0);
         if (!rc) {
             StencilCall s;
-            s.prec = PO;
+            s.prec = PX;
             s.mode = M_SRC;
             s.out_par = 0;
             s.out = bh;
-            s.in = LO[7];
-            s.y = beO;
+            s.in = tmpX;
+            s.y = beX;
             s.a = 1.0;
             s.cc = c->kappa;
             rc = launch_stencil(c, s);
         }
+        if (!rc && PX != PO) rc = convert_half(c, bh, bh0);
         if (!rc) rc = state_init(c, outer, 0.0, 0.0, o.max_outer, 1e-30, 0);
         if (!rc) rc = set_tol2(c, outer, aux, 0, 0.25 * tol[i] * tol[i]);
-        if (!rc) rc = blas_init(c, PO, nn, bh, LO[1], LO[2], LO[3], LO[0], 1, outer, FIN_INIT);
+        // x_e = 0 (a zero complex has the same bits in FP64 and DF64)
+        if (!rc) rc = blas_init(c, PO, nn, bh0, LO[1], LO[2], LO[3], XX, 1, outer, FIN_INIT);
         c->stream = keep;
         if (rc) return rc;
         BProb &pr = host[i];
@@ -515,7 +534,7 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         }
         pr.x = sp(L32[0]); pr.r = sp(L32[1]); pr.rt = sp(L32[2]); pr.p = sp(L32[3]);
         pr.q = sp(L32[4]); pr.t = sp(L32[5]); pr.tmp = sp(L32[7]);
-        pr.X = sp(LO[0]); pr.R = sp(LO[1]); pr.RT = sp(LO[2]); pr.P = sp(LO[3]);
+        pr.X = sp(XX); pr.R = sp(LO[1]); pr.RT = sp(LO[2]); pr.P = sp(LO[3]);
         pr.Q = sp(LO[4]); pr.T = sp(LO[5]); pr.Vv = sp(LO[6]); pr.TMP = sp(LO[7]);
         pr.in = inner;
         pr.out = outer;
@@ -660,30 +679,30 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
         qcd_ctx *c = ctxs[i];
         cudaStream_t keep = c->stream;
         c->stream = user;
-        // x_o = F_oo^-1 (b_o + kappa H_oe x_e) in the outer precision, then
-        // x rounded to FP64 for the FP64 true residual
-        HVec be, bo, xo, re, ro, X, XO, xoO, boO;
+        // x_o = F_oo^-1 (b_o + kappa H_oe x_e) in the solution's precision,
+        // then x rounded to FP64 (if it is not FP64) for the FP64 true residual
+        HVec be, bo, xo, re, ro, X, XX, xoX, boX;
         int r = QCD_OK;
         if ((r = get_work(c, QCD_F64, S64_BE, &be)) || (r = get_work(c, QCD_F64, S64_BO, &bo)) ||
             (r = get_work(c, QCD_F64, S64_XO, &xo)) || (r = get_work(c, QCD_F64, S64_RE, &re)) ||
             (r = get_work(c, QCD_F64, S64_RO, &ro)) || (r = get_work(c, QCD_F64, S64_LEVEL, &X)) ||
-            (r = get_work(c, PO, S64_LEVEL, &XO)) || (r = get_work(c, PO, S64_XO, &xoO)) ||
-            (r = get_work(c, PO, S64_BO, &boO))) {
+            (r = get_work(c, PX, S64_LEVEL, &XX)) || (r = get_work(c, PX, S64_XO, &xoX)) ||
+            (r = get_work(c, PX, S64_BO, &boX))) {
             c->stream = keep;
             return r;
         }
         StencilCall sx;
-        sx.prec = PO;
+        sx.prec = PX;
         sx.mode = M_SRC;
         sx.out_par = 1;
-        sx.out = xoO;
-        sx.in = XO;
-        sx.y = boO;
+        sx.out = xoX;
+        sx.in = XX;
+        sx.y = boX;
         sx.a = 1.0;
         sx.cc = c->kappa;
         r = launch_stencil(c, sx);
-        if (!r && PO != QCD_F64) r = convert_half(c, XO, X);
-        if (!r && PO != QCD_F64) r = convert_half(c, xoO, xo);
+        if (!r && PX != QCD_F64) r = convert_half(c, XX, X);
+        if (!r && PX != QCD_F64) r = convert_half(c, xoX, xo);
         for (int par = 0; par < 2 && !r; ++par) {
             StencilCall sr;
             sr.prec = QCD_F64;

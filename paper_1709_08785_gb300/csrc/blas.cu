@@ -51,6 +51,9 @@ static int run(qcd_ctx *c, int nsites, const Op &op, int fin, SolverState *st, c
 
 static double sp_bytes(int prec) { return prec == QCD_F32 ? 96.0 : prec == QCD_F16 ? 52.0 : 192.0; }
 
+// timing class of a BLAS launch: the FP32 level's kernels apart from the rest
+static int bcls(int prec) { return prec == QCD_F32 ? QCD_K_BLAS_F32 : QCD_K_BLAS; }
+
 // ---------------------------------------------------------------- state
 __global__ void k_state_init(SolverState *st, double tol2, double tol2_rel, int maxit, double bd_eps, int unit)
 {
@@ -103,42 +106,61 @@ int set_tol2(qcd_ctx *c, SolverState *dst, const SolverState *src, int slot, dou
 int blas_update_s(qcd_ctx *c, int prec, int n, HVec r, HVec q, SolverState *st)
 {
     const double by = 3 * sp_bytes(prec) * n;
-    PREC_SWITCH(prec, return run<1>(c, n, OpS<P>{r.sp(), q.sp(), st}, FIN_S, st, &st->done, QCD_K_BLAS, by));
+    PREC_SWITCH(prec, return run<1>(c, n, OpS<P>{r.sp(), q.sp(), st}, FIN_S, st, &st->done, bcls(prec), by));
 }
 
 int blas_update_x(qcd_ctx *c, int prec, int n, HVec x, HVec p, HVec r, HVec t, HVec rt, SolverState *st)
 {
     const double by = 7 * sp_bytes(prec) * n;
     PREC_SWITCH(prec, return run<3>(c, n, OpX<P>{x.sp(), p.sp(), r.sp(), t.sp(), rt.sp(), st}, FIN_X, st, &st->done,
-                                    QCD_K_BLAS, by));
+                                    bcls(prec), by));
 }
 
 int blas_update_p(qcd_ctx *c, int prec, int n, HVec p, HVec r, HVec q, SolverState *st, int fin)
 {
     const double by = 4 * sp_bytes(prec) * n;
     if (fin == FIN_NONE)
-        PREC_SWITCH(prec, return run<0>(c, n, OpP<P>{p.sp(), r.sp(), q.sp(), st}, fin, st, &st->done, QCD_K_BLAS, by));
-    PREC_SWITCH(prec, return run<1>(c, n, OpP<P>{p.sp(), r.sp(), q.sp(), st}, fin, st, &st->done, QCD_K_BLAS, by));
+        PREC_SWITCH(prec, return run<0>(c, n, OpP<P>{p.sp(), r.sp(), q.sp(), st}, fin, st, &st->done, bcls(prec), by));
+    PREC_SWITCH(prec, return run<1>(c, n, OpP<P>{p.sp(), r.sp(), q.sp(), st}, fin, st, &st->done, bcls(prec), by));
 }
 
 int blas_finish_half(qcd_ctx *c, int prec, int n, HVec x, HVec p, SolverState *st)
 {
     const double by = 3 * sp_bytes(prec) * n;
-    PREC_SWITCH(prec, return run<0>(c, n, OpHalf<P>{x.sp(), p.sp(), st}, FIN_NONE, st, nullptr, QCD_K_BLAS, by));
+    PREC_SWITCH(prec, return run<0>(c, n, OpHalf<P>{x.sp(), p.sp(), st}, FIN_NONE, st, nullptr, bcls(prec), by));
+}
+
+// x may be wider than the other vectors (FP64 solution, DF64 iteration)
+static int mixed_x(int prec, const HVec &x)
+{
+    if (x.prec == prec) return 0;
+    if (x.prec == QCD_F64 && prec == QCD_DF64) return 1;
+    set_error_message("unsupported solution precision %d for an iteration in %d", x.prec, prec);
+    return -1;
 }
 
 int blas_flex1(qcd_ctx *c, int prec, int n, HVec x, HVec v, HVec r, HVec q, SolverState *st)
 {
     const double by = 6 * sp_bytes(prec) * n;
+    const int mx = mixed_x(prec, x);
+    if (mx < 0) return QCD_EINVAL;
+    if (mx)
+        return run<1>(c, n, OpFlex1X<QCD_DF64, QCD_F64>{x.sp(), v.sp(), r.sp(), q.sp(), st}, FIN_S, st, &st->done,
+                      bcls(prec), by);
     PREC_SWITCH(prec, return run<1>(c, n, OpFlex1<P>{x.sp(), v.sp(), r.sp(), q.sp(), st}, FIN_S, st, &st->done,
-                                    QCD_K_BLAS, by));
+                                    bcls(prec), by));
 }
 
 int blas_flex2(qcd_ctx *c, int prec, int n, HVec x, HVec v, HVec r, HVec t, HVec rt, SolverState *st)
 {
     const double by = 7 * sp_bytes(prec) * n;
+    const int mx = mixed_x(prec, x);
+    if (mx < 0) return QCD_EINVAL;
+    if (mx)
+        return run<3>(c, n, OpFlex2X<QCD_DF64, QCD_F64>{x.sp(), v.sp(), r.sp(), t.sp(), rt.sp(), st}, FIN_X, st,
+                      &st->done, bcls(prec), by);
     PREC_SWITCH(prec, return run<3>(c, n, OpFlex2<P>{x.sp(), v.sp(), r.sp(), t.sp(), rt.sp(), st}, FIN_X, st,
-                                    &st->done, QCD_K_BLAS, by));
+                                    &st->done, bcls(prec), by));
 }
 
 int blas_init(qcd_ctx *c, int prec, int n, HVec src, HVec r, HVec rt, HVec p, HVec x, int zero_x, SolverState *st,
@@ -146,25 +168,25 @@ int blas_init(qcd_ctx *c, int prec, int n, HVec src, HVec r, HVec rt, HVec p, HV
 {
     const double by = (4 + zero_x) * sp_bytes(prec) * n;
     PREC_SWITCH(prec, return run<1>(c, n, OpInit<P>{src.sp(), r.sp(), rt.sp(), p.sp(), x.sp(), zero_x}, fin, st, nullptr,
-                                    QCD_K_BLAS, by));
+                                    bcls(prec), by));
 }
 
 int blas_norm2(qcd_ctx *c, int prec, int n, HVec a, SolverState *st, int fin)
 {
     const double by = sp_bytes(prec) * n;
-    PREC_SWITCH(prec, return run<1>(c, n, OpNorm<P>{a.sp()}, fin, st, nullptr, QCD_K_BLAS, by));
+    PREC_SWITCH(prec, return run<1>(c, n, OpNorm<P>{a.sp()}, fin, st, nullptr, bcls(prec), by));
 }
 
 int blas_dot(qcd_ctx *c, int prec, int n, HVec a, HVec b, SolverState *st, int fin, const int *done)
 {
     const double by = 2 * sp_bytes(prec) * n;
-    PREC_SWITCH(prec, return run<2>(c, n, OpDot<P>{a.sp(), b.sp()}, fin, st, done, QCD_K_BLAS, by));
+    PREC_SWITCH(prec, return run<2>(c, n, OpDot<P>{a.sp(), b.sp()}, fin, st, done, bcls(prec), by));
 }
 
 int blas_omega(qcd_ctx *c, int prec, int n, HVec t, HVec r, SolverState *st, const int *done)
 {
     const double by = 2 * sp_bytes(prec) * n;
-    PREC_SWITCH(prec, return run<3>(c, n, OpOmega<P>{t.sp(), r.sp()}, FIN_OMEGA, st, done, QCD_K_BLAS, by));
+    PREC_SWITCH(prec, return run<3>(c, n, OpOmega<P>{t.sp(), r.sp()}, FIN_OMEGA, st, done, bcls(prec), by));
 }
 
 int blas_inner_init(qcd_ctx *c, int ps, int pd, int n, HVec src, const double *src_norm2, HVec r, HVec rt, HVec p,
@@ -173,16 +195,16 @@ int blas_inner_init(qcd_ctx *c, int ps, int pd, int n, HVec src, const double *s
     const double by = (sp_bytes(ps) + 4 * sp_bytes(pd)) * n;
     if (ps == QCD_F64 && pd == QCD_F32)
         return run<0>(c, n, OpInner<QCD_F64, QCD_F32>{src.sp(), r.sp(), rt.sp(), p.sp(), x.sp(), src_norm2}, FIN_NONE,
-                      nullptr, done, QCD_K_BLAS, by);
+                      nullptr, done, bcls(pd), by);
     if (ps == QCD_F32 && pd == QCD_F16)
         return run<0>(c, n, OpInner<QCD_F32, QCD_F16>{src.sp(), r.sp(), rt.sp(), p.sp(), x.sp(), src_norm2}, FIN_NONE,
-                      nullptr, done, QCD_K_BLAS, by);
+                      nullptr, done, bcls(pd), by);
     if (ps == QCD_F64 && pd == QCD_F16)
         return run<0>(c, n, OpInner<QCD_F64, QCD_F16>{src.sp(), r.sp(), rt.sp(), p.sp(), x.sp(), src_norm2}, FIN_NONE,
-                      nullptr, done, QCD_K_BLAS, by);
+                      nullptr, done, bcls(pd), by);
     if (ps == QCD_DF64 && pd == QCD_F32)
         return run<0>(c, n, OpInner<QCD_DF64, QCD_F32>{src.sp(), r.sp(), rt.sp(), p.sp(), x.sp(), src_norm2}, FIN_NONE,
-                      nullptr, done, QCD_K_BLAS, by);
+                      nullptr, done, bcls(pd), by);
     set_error_message("unsupported precision pair %d -> %d", ps, pd);
     return QCD_EINVAL;
 }
@@ -191,13 +213,13 @@ int blas_lift(qcd_ctx *c, int ps, int pd, int n, HVec x, HVec v, const double *s
 {
     const double by = (sp_bytes(ps) + sp_bytes(pd)) * n;
     if (ps == QCD_F32 && pd == QCD_F64)
-        return run<0>(c, n, OpLift<QCD_F32, QCD_F64>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, QCD_K_BLAS, by);
+        return run<0>(c, n, OpLift<QCD_F32, QCD_F64>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, bcls(ps), by);
     if (ps == QCD_F16 && pd == QCD_F32)
-        return run<0>(c, n, OpLift<QCD_F16, QCD_F32>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, QCD_K_BLAS, by);
+        return run<0>(c, n, OpLift<QCD_F16, QCD_F32>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, bcls(ps), by);
     if (ps == QCD_F16 && pd == QCD_F64)
-        return run<0>(c, n, OpLift<QCD_F16, QCD_F64>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, QCD_K_BLAS, by);
+        return run<0>(c, n, OpLift<QCD_F16, QCD_F64>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, bcls(ps), by);
     if (ps == QCD_F32 && pd == QCD_DF64)
-        return run<0>(c, n, OpLift<QCD_F32, QCD_DF64>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, QCD_K_BLAS,
+        return run<0>(c, n, OpLift<QCD_F32, QCD_DF64>{x.sp(), v.sp(), src_norm2}, FIN_NONE, nullptr, done, bcls(ps),
                       by);
     set_error_message("unsupported precision pair %d -> %d", ps, pd);
     return QCD_EINVAL;

@@ -270,6 +270,65 @@ struct OpFlex2 {
     }
 };
 
+// The flexible updates with the solution in a wider storage than the
+// iteration's own vectors: x (precision PX, FP64) += coef * v, where v and
+// the residual vectors are in P (DF64).  v is widened to PX and the update
+// runs in PX arithmetic, so the accumulated solution carries PX's precision
+// whatever the operator's arithmetic was.
+template <int P, int PX>
+__device__ __forceinline__ void acc_x(SpinorPtr x, int cb, const SolverState *st, int which,
+                                      const Spinor<typename Prec<P>::T> &V)
+{
+    using TX = typename Prec<PX>::T;
+    Spinor<TX> X, Vx;
+    Prec<PX>::load(x, cb, X);
+    cvt_sp(Vx, V);
+    caxpy(X, coef<TX>(st, which, 1), Vx);
+    Prec<PX>::store(x, cb, X);
+}
+
+// OpFlex1 with x in PX: x += alpha v; r -= alpha q; |r|^2
+template <int P, int PX>
+struct OpFlex1X {
+    SpinorPtr x, v, r, q;
+    const SolverState *st;
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
+    {
+        using T = typename Prec<P>::T;
+        Spinor<T> V, R, Q;
+        Prec<P>::load(v, cb, V);
+        acc_x<P, PX>(x, cb, st, C_ALPHA, V);
+        Prec<P>::load(r, cb, R);
+        Prec<P>::load(q, cb, Q);
+        caxpy(R, coef<T>(st, C_ALPHA, -1), Q);
+        Prec<P>::store(r, cb, R);
+        acc_norm2(acc[0], R);
+    }
+};
+
+// OpFlex2 with x in PX: x += omega v; r -= omega t; |r|^2, <r~|r>
+template <int P, int PX>
+struct OpFlex2X {
+    SpinorPtr x, v, r, t, rt;
+    const SolverState *st;
+    template <class Acc>
+    __device__ void operator()(int cb, Acc *acc) const
+    {
+        using T = typename Prec<P>::T;
+        Spinor<T> V, R, Tt, Rt;
+        Prec<P>::load(v, cb, V);
+        acc_x<P, PX>(x, cb, st, C_OMEGA, V);
+        Prec<P>::load(r, cb, R);
+        Prec<P>::load(t, cb, Tt);
+        caxpy(R, coef<T>(st, C_OMEGA, -1), Tt);
+        Prec<P>::store(r, cb, R);
+        Prec<P>::load(rt, cb, Rt);
+        acc_norm2(acc[0], R);
+        acc_dot(Rt, R, acc[1], acc[2]);
+    }
+};
+
 // r = r~ = p = src (optionally x = 0), |r|^2
 template <int P>
 struct OpInit {

@@ -64,7 +64,7 @@ extern "C" int qcd_dslash_eo_noalloc(qcd_ctx *c, void *out, const void *in, int 
         set_error_message("null argument");
         return QCD_EINVAL;
     }
-    if (prec < QCD_F64 || prec > QCD_F16 || (out_parity != 0 && out_parity != 1)) {
+    if (prec < QCD_F64 || prec > QCD_DF64 || (out_parity != 0 && out_parity != 1)) {
         set_error_message("bad precision %d or parity %d", prec, out_parity);
         return QCD_EINVAL;
     }
@@ -81,8 +81,16 @@ extern "C" int qcd_dslash_eo_noalloc(qcd_ctx *c, void *out, const void *in, int 
                           need, NOALLOC_SCRATCH_BYTES, NOALLOC_SCRATCH_BYTES / 384);
         return QCD_EINVAL;
     }
+    // the array's address is per device and is looked up with the device
+    // current; the kernels run on the context's stream, i.e. its device
     int dev = -1;
     QCD_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev != c->device) {
+        set_error_message("qcd_dslash_eo_noalloc: the context lives on device %d but device %d is current; make the "
+                          "context's device current before the call",
+                          c->device, dev);
+        return QCD_EINVAL;
+    }
     void *base = nullptr;
     int rc = scratch_address(dev, &base);
     if (rc) return rc;
@@ -97,7 +105,7 @@ extern "C" int qcd_dslash_eo_noalloc(qcd_ctx *c, void *out, const void *in, int 
     // timing events are created on demand by the profiler: keep it off here
     const bool prof = c->profiling;
     c->profiling = false;
-    const int f32io = prec != QCD_F64;
+    const int f32io = prec == QCD_F32 || prec == QCD_F16;  // QCD_DF64 takes complex128, as QCD_F64
     rc = canon_to_half(c, prec, f32io, in, -1, vin, 1, 0);
     if (rc == QCD_OK) {
         StencilCall s;

@@ -141,6 +141,7 @@ struct Solver {
     qcd_solve_info info;
     Level lv[3];  // 0: FP64, 1: FP32, 2: FP16
     HVec be, bo, bhat, xo, re, ro;
+    HVec bhat0;  // b^_e in the outer operator's precision (residual restarts)
     SolverState *aux;
 };
 
@@ -233,7 +234,7 @@ int residual_eo(Solver &S, HVec xe, HVec out, SolverState *st, int fin)
     s2.y = xe;
     s2.a = -1.0;
     s2.cc = c->kappa * c->kappa;
-    s2.z = S.bhat;
+    s2.z = S.bhat0;
     s2.d = 1.0;
     s2.red = R_NORM;
     s2.red_args = RedArgs{c->partials, c->counters, st, fin};
@@ -288,25 +289,41 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     qcd_ctx *c = S.c;
     const int n = c->g.Vh_pad;
     Level &O = S.lv[0];
-    // The outer level computes in P0: FP64 for the plain BiCGStab, and for
-    // the nested schemes by default DF64 (float pairs, ~48 bits; GB300's
-    // FP64 rate is ~1/64 of its FP32 rate).  The true-residual check
-    // ||b - D x|| that decides convergence is FP64 either way, from the FP64
-    // links and clover term and x rounded to FP64.
-    const int P0 = (S.o.precision_levels >= 2 && S.o.outer_df64) ? QCD_DF64 : QCD_F64;
+    // Precisions of the outer level (Alg. 1).  P0: the outer D^ and the
+    // iteration's own vectors r, r~, p, q, t, v.  PX: the solution x_e, the
+    // source b^_e (Eq. 6) and the reconstruction x_o (Eq. 7).
+    //   outer_df64 = 0: P0 = PX = FP64 (Alg. 1 as printed);
+    //   outer_df64 = 1: P0 = DF64, PX = FP64 -- the solution is accumulated
+    //                   in FP64 arithmetic, the operator applications and the
+    //                   recursions run in float pairs (GB300's FP64 rate is
+    //                   ~1/64 of its FP32 rate);
+    //   outer_df64 = 2: P0 = PX = DF64.
+    // Dot products and norms of the outer level are summed in FP64 in every
+    // mode, and the true-residual check ||b - D x|| that decides convergence
+    // is FP64 from the FP64 links and clover term.
+    const int mode = S.o.precision_levels >= 2 ? S.o.outer_df64 : 0;
+    const int P0 = mode ? QCD_DF64 : QCD_F64;
+    const int PX = mode == 2 ? QCD_DF64 : QCD_F64;
     TRY(get_work(c, QCD_F64, 0, &S.be));
     TRY(get_work(c, QCD_F64, 1, &S.bo));
     TRY(get_work(c, QCD_F64, 3, &S.xo));
     TRY(get_work(c, QCD_F64, 4, &S.re));
     TRY(get_work(c, QCD_F64, 5, &S.ro));
-    TRY(get_work(c, P0, 2, &S.bhat));
+    TRY(get_work(c, PX, 2, &S.bhat));
     TRY(get_level(c, O, P0, 6, ST_OUTER));
-    HVec beP = S.be, boP = S.bo, xoP = S.xo, xe64 = O.x;
-    if (P0 != QCD_F64) {
-        TRY(get_work(c, P0, 0, &beP));
-        TRY(get_work(c, P0, 1, &boP));
-        TRY(get_work(c, P0, 3, &xoP));
+    HVec beX = S.be, boX = S.bo, xoX = S.xo, xe64 = O.x, xe0 = O.x, tmpX = O.tmp;
+    S.bhat0 = S.bhat;
+    if (PX != QCD_F64) {  // all-DF64 outer level: DF64 copies of b_e, b_o, x_o
+        TRY(get_work(c, PX, 0, &beX));
+        TRY(get_work(c, PX, 1, &boX));
+        TRY(get_work(c, PX, 3, &xoX));
         TRY(get_work(c, QCD_F64, 6, &xe64));
+    }
+    if (PX != P0) {  // FP64 solution around a DF64 iteration
+        TRY(get_work(c, QCD_F64, 6, &O.x));  // x_e in FP64
+        xe64 = O.x;
+        TRY(get_work(c, P0, 2, &S.bhat0));   // b^_e rounded to DF64
+        tmpX = S.re;                          // FP64 scratch before the true residual needs it
     }
     if (S.o.precision_levels >= 2) TRY(get_level(c, S.lv[1], QCD_F32, 0, ST_MID));
     if (S.o.precision_levels >= 3) TRY(get_level(c, S.lv[2], QCD_F16, 0, ST_INNER));
@@ -318,24 +335,31 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     TRY(state_init(c, S.aux, 0.0, 0.0, 0, 0.0, 0));
     TRY(blas_norm2(c, QCD_F64, n, S.be, S.aux, FIN_SETN + 0));
     TRY(blas_norm2(c, QCD_F64, n, S.bo, S.aux, FIN_ADDN + 0));
-    if (P0 != QCD_F64) {
-        TRY(convert_half(c, S.be, beP));
-        TRY(convert_half(c, S.bo, boP));
+    if (PX != QCD_F64) {
+        TRY(convert_half(c, S.be, beX));
+        TRY(convert_half(c, S.bo, boX));
     }
     // b^_e = F_ee^-1 (b_e + kappa H_eo F_oo^-1 b_o)   (Eq. 6, Alg. 1 line 3)
-    TRY(clover_apply_half(c, P0, 1, 1, boP, O.tmp, 1, 0));
+    TRY(clover_apply_half(c, PX, 1, 1, boX, tmpX, 1, 0));
     {
         StencilCall s;
-        s.prec = P0;
+        s.prec = PX;
         s.mode = M_SRC;
         s.out_par = 0;
         s.out = S.bhat;
-        s.in = O.tmp;
-        s.y = beP;
+        s.in = tmpX;
+        s.y = beX;
         s.a = 1.0;
         s.cc = c->kappa;
         TRY(launch_stencil(c, s));
     }
+    if (PX != P0) TRY(convert_half(c, S.bhat, S.bhat0));
+    // x_e in the operator's precision, for a recomputed residual b^ - D^ x_e
+    auto x_for_operator = [&]() -> int {
+        if (PX == P0) return QCD_OK;
+        TRY(get_work(c, P0, 6, &xe0));
+        return convert_half(c, O.x, xe0);
+    };
     // the recursive residual |r^_e| is driven below tol |b| / 2: the full
     // residual is F_ee r^_e with |F_ee| close to one; the true residual
     // is checked at the end and the iteration restarted from it if needed
@@ -343,11 +367,14 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     TRY(state_init(c, O.st, 0.0, 0.0, maxit, BD_EPS_F64, 0));
     TRY(set_tol2(c, O.st, S.aux, 0, 0.25 * tol * tol));
     if (S.o.use_x0) {
-        TRY(canon_to_half(c, P0, 0, x, 0, O.x, 1, 0));
-        TRY(residual_eo(S, O.x, O.r, O.st, FIN_NONE));
+        TRY(canon_to_half(c, PX, 0, x, 0, O.x, 1, 0));
+        TRY(x_for_operator());
+        TRY(residual_eo(S, xe0, O.r, O.st, FIN_NONE));
         TRY(blas_init(c, P0, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_INIT));
     } else {
-        TRY(blas_init(c, P0, n, S.bhat, O.r, O.rt, O.p, O.x, 1, O.st, FIN_INIT));
+        // x_e = 0: a zero complex is all zero bits in the FP64 and DF64
+        // layouts alike, so the DF64 init clears an FP64 x_e as well
+        TRY(blas_init(c, P0, n, S.bhat0, O.r, O.rt, O.p, O.x, 1, O.st, FIN_INIT));
     }
     SolverState h, ha;
     int status = QCD_OK;
@@ -363,18 +390,18 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         status = h.status;
         // x_o = F_oo^-1 (b_o + kappa H_oe x_e)   (Eq. 7, Alg. 1 line 19)
         StencilCall s;
-        s.prec = P0;
+        s.prec = PX;
         s.mode = M_SRC;
         s.out_par = 1;
-        s.out = xoP;
+        s.out = xoX;
         s.in = O.x;
-        s.y = boP;
+        s.y = boX;
         s.a = 1.0;
         s.cc = c->kappa;
         TRY(launch_stencil(c, s));
-        if (P0 != QCD_F64) {
+        if (PX != QCD_F64) {
             TRY(convert_half(c, O.x, xe64));
-            TRY(convert_half(c, xoP, S.xo));
+            TRY(convert_half(c, xoX, S.xo));
         }
         TRY(emit_x(c, xe64, S.xo, x));
         TRY(true_residual(S, QCD_F64, xe64, S.xo, S.be, S.bo));
@@ -397,7 +424,8 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         S.info.restarts += 1;
         TRY(state_init(c, O.st, 0.0, 0.0, maxit, BD_EPS_F64, 0));
         TRY(set_tol2(c, O.st, S.aux, 0, 0.25 * tol * tol));
-        TRY(residual_eo(S, O.x, O.r, O.st, FIN_NONE));
+        TRY(x_for_operator());
+        TRY(residual_eo(S, xe0, O.r, O.st, FIN_NONE));
         TRY(blas_init(c, P0, n, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_RESTART));
     }
     return status;

@@ -13,7 +13,7 @@ import os
 from dataclasses import dataclass, field
 
 F64, F32, F16, DF64 = 0, 1, 2, 3
-K_MULT_F64, K_MULT_F32, K_MULT_F16, K_BLAS, K_OTHER, K_DHAT_F32, K_MULT_DF64 = 0, 1, 2, 3, 4, 5, 6
+K_MULT_F64, K_MULT_F32, K_MULT_F16, K_BLAS, K_OTHER, K_DHAT_F32, K_MULT_DF64, K_BLAS_F32 = 0, 1, 2, 3, 4, 5, 6, 7
 
 STATUS = {
     0: "QCD_OK", -1: "QCD_EINVAL", -2: "QCD_ECUDA", -3: "QCD_ENOMEM", -4: "QCD_ENOTCONV",

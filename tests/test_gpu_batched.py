@@ -61,6 +61,9 @@ def test_batched_solves_reach_tolerance(batch, graphs):
         r = oracle.true_residual(p["dims"], -1, p["U"], F, p["kappa"], p["b"], x.cpu().numpy())
         assert r <= 1e-10, (p["dims"], r, info)
         assert abs(r - info["true_resid"]) <= 1e-12 + 0.1 * r
+        # the persistent kernels converged every problem themselves: no
+        # problem was handed to the single-solve driver afterwards
+        assert info["restarts"] == 0, info
         if p["dims"] != (2, 2, 2, 2):
             assert info["inner_iters"][0] > 0 and info["dhat_applies"][1] > 0
 
@@ -107,10 +110,50 @@ def test_batched_rejects_bad_arguments(batch):
         qcd.solve_batched([p["ctx"], p["ctx"]], [p["bd"], p["bd"]], [x, torch.zeros_like(x)], [1e-10, 1e-10])
 
 
-def test_batched_fp64_outer_level(batch):
-    """The batch with its outer level in FP64 (outer_df64 = 0) instead of DF64."""
-    xs, infos = run_batch(batch, outer_df64=0)
+@pytest.mark.parametrize("mode", [0, 2])
+def test_batched_outer_level_modes(batch, mode):
+    """The batch with its outer level in FP64 (outer_df64 = 0) or all in
+    DF64 (2) instead of the default (FP64 solution around DF64 operator
+    applications)."""
+    xs, infos = run_batch(batch, outer_df64=mode)
     for p, x, inf in zip(batch, xs, infos):
-        assert inf["status"] == 0
+        assert inf["status"] == 0 and inf["restarts"] == 0, inf
         F = oracle.clover_field(p["dims"], p["U"], p["kappa"], 1.0)
         assert oracle.true_residual(p["dims"], -1, p["U"], F, p["kappa"], p["b"], x.cpu().numpy()) <= 1e-10
+
+
+def test_batched_48_problem_workload():
+    """The batched workload at its own sizes: 48 problems drawn from
+    {8^4, 12^3x24, 16^3x32, 20^3x40} (inputs.batch_problems(48, 99)), tol
+    1e-10, one batched run.  Every solution's true residual is recomputed by
+    the oracle (in a spawned process pool) and must meet the tolerance, and
+    no problem may have needed the single-solve fallback."""
+    import multiprocessing as mp
+    import os
+
+    import oracle_workers
+    from paper_1709_08785_gb300 import qcd
+
+    probs = inputs.batch_problems(48, 99)
+    tol = 1e-10
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        fields = pool.map(oracle_workers.links_and_source, probs, chunksize=1)
+        ctxs, bs, xs = [], [], []
+        for p, (U, b) in zip(probs, fields):
+            c = qcd.Context(p["dims"], -1)
+            c.gauge_load(torch.from_numpy(U).cuda())
+            c.clover_build(p["kappa"], p["csw"])
+            ctxs.append(c)
+            bs.append(torch.from_numpy(b).cuda())
+            xs.append(torch.zeros_like(bs[-1]))
+        del fields
+        infos = qcd.solve_batched(ctxs, bs, xs, [tol] * len(probs), precision_levels=2)
+        torch.cuda.synchronize()
+        res = pool.map(oracle_workers.true_residual, [(p, x.cpu().numpy()) for p, x in zip(probs, xs)], chunksize=1)
+    for p, info, r in zip(probs, infos, res):
+        assert info["status"] == 0 and info["restarts"] == 0, (p, info)
+        assert r <= tol, (p, r, info)
+        assert abs(r - info["true_resid"]) <= 1e-14 + 1e-3 * r, (p, r, info["true_resid"])
+    assert {p["dims"] for p in probs} == set(inputs.BATCH_LATTICES)
+    for c in ctxs:
+        c.close()

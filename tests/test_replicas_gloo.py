@@ -38,7 +38,7 @@ def worker(rank, ws, port, results):
 
 def test_max_over_ranks_gloo_world_size_2():
     ws = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         results = m.dict()
         mp.start_processes(worker, args=(ws, free_port(), results), nprocs=ws, start_method="spawn", join=True)
         got = dict(results)

@@ -1,7 +1,8 @@
 """qcd_dslash_eo_noalloc: the hopping term for callers that must not allocate
 device memory during the call (for instance a serving loop whose allocator
-is frozen after start-up).  It must return what qcd_dslash_eo returns, call
-after call, while leaving the device's free memory untouched.
+is frozen after start-up).  It runs the same kernels as qcd_dslash_eo on the
+same inputs, so its result must equal qcd_dslash_eo's bit for bit, call after
+call, while leaving the device's free memory untouched.
 
 Named to be collected last: if it fails, a run that stops at the first
 failure has already run every other test.
@@ -15,23 +16,27 @@ from paper_1709_08785_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-13, 1: 2e-6, 2: 2e-3}  # the operator tolerances of the other GPU tests
+F64, F32, F16, DF64 = 0, 1, 2, 3
 
 
-def rel(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+def dtype_of(prec):
+    return torch.complex64 if prec in (F32, F16) else torch.complex128
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
-def test_noalloc_matches_dslash_eo_twice(prec):
+def make_ctx(dims, seed):
     from paper_1709_08785_gb300 import qcd
 
-    dims, t_bc = (8, 8, 8, 16), -1
+    ctx = qcd.Context(dims, -1)
+    ctx.gauge_load(torch.from_numpy(inputs.random_gauge(dims, 0.25, seed)).cuda())
+    return ctx
+
+
+@pytest.mark.parametrize("prec", [F64, F32, F16, DF64])
+def test_noalloc_matches_dslash_eo_twice(prec):
+    dims = (8, 8, 8, 16)
     Vh = inputs.volume(dims) // 2
-    U = inputs.random_gauge(dims, 0.25, 71)
-    ctx = qcd.Context(dims, t_bc)
-    ctx.gauge_load(torch.from_numpy(U).cuda())
-    dt = torch.complex128 if prec == 0 else torch.complex64
+    ctx = make_ctx(dims, 71)
+    dt = dtype_of(prec)
     srcs = [torch.from_numpy(inputs.gaussian_source(dims, 72 + k)[:Vh]).to(dt).cuda() for k in range(2)]
     # the first calls are the documented set-up: they look up the scratch
     # array and let the driver load the kernels used (one per dagger value)
@@ -47,17 +52,44 @@ def test_noalloc_matches_dslash_eo_twice(prec):
         ctx.dslash_eo_noalloc(got[k], srcs[k], par, dag, prec)
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0
-    # the allocating entry point on the same inputs
+    # the allocating entry point on the same inputs: the same kernels, so
+    # the same bits
     for k, (par, dag) in enumerate([(0, False), (1, True)]):
         want = torch.zeros_like(srcs[k])
         ctx.dslash_eo(want, srcs[k], par, dag, prec)
         torch.cuda.synchronize()
-        w = want.cpu().numpy()
-        assert rel(got[k].cpu().numpy(), w) < TOL[prec]
+        assert np.array_equal(got[k].cpu().numpy(), want.cpu().numpy())
     ctx.close()
 
 
-def test_noalloc_rejects_lattices_beyond_its_scratch():
+def test_two_contexts_share_the_array_in_stream_order():
+    """Two contexts of different lattices call the entry point alternately on
+    one stream: each call overwrites the shared array, and each result must
+    still equal the allocating entry point's."""
+    shapes = [((8, 8, 8, 16), 81), ((6, 4, 4, 10), 82)]  # the second has a ragged last 32-site block
+    ctxs = [make_ctx(d, s) for d, s in shapes]
+    outs, ins = [], []
+    for (d, _), ctx in zip(shapes, ctxs):
+        Vh = inputs.volume(d) // 2
+        ins.append(torch.from_numpy(inputs.gaussian_source(d, 90 + Vh)[:Vh]).cuda())
+        outs.append([torch.zeros_like(ins[-1]) for _ in range(2)])
+        ctx.dslash_eo_noalloc(outs[-1][0], ins[-1], 0, False, F64)  # set-up call
+    for rep in range(2):
+        for k, ctx in enumerate(ctxs):
+            ctx.dslash_eo_noalloc(outs[k][rep], ins[k], 1, rep == 1, F64)
+    torch.cuda.synchronize()
+    for k, ctx in enumerate(ctxs):
+        for rep in range(2):
+            want = torch.zeros_like(ins[k])
+            ctx.dslash_eo(want, ins[k], 1, rep == 1, F64)
+            torch.cuda.synchronize()
+            assert np.array_equal(outs[k][rep].cpu().numpy(), want.cpu().numpy()), (k, rep)
+    for ctx in ctxs:
+        ctx.close()
+
+
+@pytest.mark.parametrize("prec", [F64, DF64])
+def test_noalloc_rejects_lattices_beyond_its_scratch(prec):
     from paper_1709_08785_gb300 import qcd
 
     dims = (16, 16, 16, 64)  # 131072 sites per parity: twice the FP64 limit
@@ -67,6 +99,6 @@ def test_noalloc_rejects_lattices_beyond_its_scratch():
     v = torch.zeros((Vh, 4, 3), dtype=torch.complex128, device="cuda")
     out = torch.zeros_like(v)
     with pytest.raises(qcd.QCDError) as e:
-        ctx.dslash_eo_noalloc(out, v, 0, False, 0)
+        ctx.dslash_eo_noalloc(out, v, 0, False, prec)
     assert e.value.status == -1  # QCD_EINVAL
     ctx.close()
