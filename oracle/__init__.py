@@ -242,6 +242,25 @@ def dhat(dims, t_bc, U, Finv, kappa, p):
     return q
 
 
+def schur_ee(dims, t_bc, U, F, Finv, kappa, p):
+    """S_ee p = F_ee p - kappa^2 H_eo F_oo^-1 H_oe p: the gamma5-hermitian
+    even-odd operator, F_ee times D^_ee of Eq. 8."""
+    U, F, Finv, p = _c(U), _c(F), _c(Finv), _c(p)
+    q = np.empty_like(p)
+    lib().oracle_schur_ee(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(F), _p(Finv), ctypes.c_double(kappa), _p(p),
+                          _p(q))
+    return q
+
+
+def schur_source(dims, t_bc, U, Finv, kappa, b):
+    """The right-hand side of S_ee x_e: b_e + kappa H_eo F_oo^-1 b_o."""
+    U, Finv, b = _c(U), _c(Finv), _c(b)
+    out = np.empty((volume(dims) // 2, 4, 3), dtype=np.complex128)
+    lib().oracle_schur_source(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(Finv), ctypes.c_double(kappa), _p(b),
+                              _p(out))
+    return out
+
+
 def eo_source(dims, t_bc, U, Finv, kappa, b):
     """b^_e = F_ee^-1 b_e + kappa H~_eo F_oo^-1 b_o (Eq. 6)."""
     U, Finv, b = _c(U), _c(Finv), _c(b)
@@ -284,6 +303,17 @@ def bicgstab_eo(dims, t_bc, U, Finv, kappa, b, tol_eo, maxit=10000):
     it = ctypes.c_int(0)
     st = lib().oracle_bicgstab_eo(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(Finv), ctypes.c_double(kappa), _p(b),
                                   _p(x), ctypes.c_double(tol_eo), ctypes.c_int(maxit), ctypes.byref(it))
+    return x, st, it.value
+
+
+def bicgstab_schur(dims, t_bc, U, F, Finv, kappa, b, tol_eo, maxit=10000):
+    """FP64 BiCGStab on the gamma5-hermitian S_ee, then x_o (Eq. 7); returns
+    (x_full, status, iters)."""
+    U, F, Finv, b = _c(U), _c(F), _c(Finv), _c(b)
+    x = np.empty_like(b)
+    it = ctypes.c_int(0)
+    st = lib().oracle_bicgstab_schur(_dims(dims), ctypes.c_int(t_bc), _p(U), _p(F), _p(Finv), ctypes.c_double(kappa),
+                                     _p(b), _p(x), ctypes.c_double(tol_eo), ctypes.c_int(maxit), ctypes.byref(it))
     return x, st, it.value
 
 

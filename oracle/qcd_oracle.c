@@ -21,6 +21,9 @@
  *     b^_e and x_o                                      (Sec. II-B, Eqs. 5-9;
  *     the printed "H~_eo H~_eo" is read as H~_eo H~_oe, the only product the
  *     Schur complement of D allows)
+ *   - the gamma5-hermitian even-odd operator S_ee = F_ee - kappa^2 H_eo
+ *     F_oo^-1 H_oe (the Schur complement of D on the even sites, i.e.
+ *     F_ee D^_ee) with its source b_e + kappa H_eo F_oo^-1 b_o
  *   - BiCGStab: Alg. 2, and the flexible nested form of Alg. 1, with
  *     alpha = rho0/<r~|q> and beta = (rho1/rho0)(alpha/omega) (the printed
  *     alpha = <r~|q> and beta = (rho1/rho0)/(alpha/omega) are read as the
@@ -568,6 +571,27 @@ typedef struct {
     double kappa;
 } eo_op;
 
+/* M(n) in(n) at the sites of parity p, M a full field of 12x12 site
+ * matrices (the clover term F or its inverse), in/out half vectors */
+static void site_matrix_half(const int L[4], const double *M_, int parity, const double *in_, double *out_)
+{
+    const cplx *Fi = (const cplx *)M_;
+    const cplx *in = (const cplx *)in_;
+    cplx *out = (cplx *)out_;
+    long V = vol(L);
+    SITE_LOOP
+    for (long cb = 0; cb < V / 2; ++cb) {
+        long s = site_of_cb(L, parity, cb);
+        cplx t[12];
+        for (int a = 0; a < 12; ++a) {
+            cplx acc = 0;
+            for (int b = 0; b < 12; ++b) acc += Fi[s * 144 + a * 12 + b] * in[cb * 12 + b];
+            t[a] = acc;
+        }
+        memcpy(out + cb * 12, t, sizeof(t));
+    }
+}
+
 /* F_pp^-1 applied to a half vector of parity p */
 static void clover_inv_half(const eo_op *op, int parity, const double *in_, double *out_)
 {
@@ -622,6 +646,54 @@ void oracle_dhat(const int L[4], int t_bc, const double *U, const double *Finv, 
 {
     eo_op op = {{L[0], L[1], L[2], L[3]}, t_bc, U, Finv, NULL, kappa};
     dhat(&op, p, q);
+}
+
+/* The gamma5-hermitian even-odd operator: the Schur complement of D on the
+ * even sites itself,
+ *     S_ee = F_ee - kappa^2 H_eo F_oo^-1 H_oe       (Sec. II-B, Eqs. 5-8),
+ * i.e. D^_ee of Eq. 8 before its left factor F_ee^-1 (D^_ee = F_ee^-1 S_ee).
+ * F is the full clover field and Finv its inverse, both [V][12][12]. */
+static void schur_ee(const eo_op *op, const double *p_, double *q_)
+{
+    long Vh = vol(op->L) / 2;
+    double *ho = malloc(sizeof(cplx) * 12 * Vh);   /* H_oe p */
+    double *fo = malloc(sizeof(cplx) * 12 * Vh);   /* F_oo^-1 H_oe p */
+    double *he = malloc(sizeof(cplx) * 12 * Vh);   /* H_eo F_oo^-1 H_oe p */
+    double *fe = malloc(sizeof(cplx) * 12 * Vh);   /* F_ee p */
+    oracle_hop_eo(op->L, op->t_bc, op->U, 1, p_, ho, 0);
+    site_matrix_half(op->L, op->Finv, 1, ho, fo);
+    oracle_hop_eo(op->L, op->t_bc, op->U, 0, fo, he, 0);
+    site_matrix_half(op->L, op->F, 0, p_, fe);
+    cplx *q = (cplx *)q_;
+    const cplx *a = (const cplx *)fe, *h = (const cplx *)he;
+    double k2 = op->kappa * op->kappa;
+    for (long i = 0; i < 12 * Vh; ++i) q[i] = a[i] - k2 * h[i];
+    free(ho); free(fo); free(he); free(fe);
+}
+
+void oracle_schur_ee(const int L[4], int t_bc, const double *U, const double *F, const double *Finv, double kappa,
+                     const double *p, double *q)
+{
+    eo_op op = {{L[0], L[1], L[2], L[3]}, t_bc, U, Finv, F, kappa};
+    schur_ee(&op, p, q);
+}
+
+/* Its right-hand side: with b = D x, S_ee x_e = b_e + kappa H_eo F_oo^-1 b_o
+ * (the even rows of D x = b with x_o eliminated through the odd rows) */
+void oracle_schur_source(const int L[4], int t_bc, const double *U, const double *Finv, double kappa,
+                         const double *b_full, double *src_e_)
+{
+    long Vh = vol(L) / 2;
+    double *be = malloc(sizeof(cplx) * 12 * Vh), *bo = malloc(sizeof(cplx) * 12 * Vh);
+    double *fo = malloc(sizeof(cplx) * 12 * Vh), *he = malloc(sizeof(cplx) * 12 * Vh);
+    oracle_full_to_half(L, 0, b_full, be);
+    oracle_full_to_half(L, 1, b_full, bo);
+    site_matrix_half(L, Finv, 1, bo, fo);        /* F_oo^-1 b_o */
+    oracle_hop_eo(L, t_bc, U, 0, fo, he, 0);     /* H_eo F_oo^-1 b_o */
+    cplx *o = (cplx *)src_e_;
+    const cplx *a = (const cplx *)be, *h = (const cplx *)he;
+    for (long i = 0; i < 12 * Vh; ++i) o[i] = a[i] + kappa * h[i];
+    free(be); free(bo); free(fo); free(he);
 }
 
 /* b^_e = F_ee^-1 b_e + kappa H~_eo F_oo^-1 b_o  (Eq. 6) */
@@ -793,6 +865,26 @@ int oracle_bicgstab_eo(const int L[4], int t_bc, const double *U, const double *
     oracle_eo_reconstruct(L, t_bc, U, Finv, kappa, b_full, (const double *)xe, x_full);
     if (iters_out) *iters_out = st.iters;
     free(bh); free(xe);
+    return st.status;
+}
+
+static void apply_schur(const void *ctx, const double *in, double *out) { schur_ee((const eo_op *)ctx, in, out); }
+
+/* FP64 BiCGStab on the gamma5-hermitian operator S_ee: its source, the
+ * solve (exit on ||r|| < tol_eo ||src||), and x_o as for D^_ee (Eq. 7). */
+int oracle_bicgstab_schur(const int L[4], int t_bc, const double *U, const double *F, const double *Finv,
+                          double kappa, const double *b_full, double *x_full, double tol_eo, int maxit,
+                          int *iters_out)
+{
+    eo_op op = {{L[0], L[1], L[2], L[3]}, t_bc, U, Finv, F, kappa};
+    long Vh = vol(L) / 2, n = 12 * Vh;
+    cplx *src = malloc(sizeof(cplx) * n), *xe = calloc(n, sizeof(cplx));
+    oracle_schur_source(L, t_bc, U, Finv, kappa, b_full, (double *)src);
+    solve_stats st;
+    bicgstab(apply_schur, &op, n, src, xe, tol_eo * sqrt(vnorm2(n, src)), maxit, &st);
+    oracle_eo_reconstruct(L, t_bc, U, Finv, kappa, b_full, (const double *)xe, x_full);
+    if (iters_out) *iters_out = st.iters;
+    free(src); free(xe);
     return st.status;
 }
 

@@ -11,6 +11,8 @@ of them:
   planes gives F = 1 - csw*kappa*sigma_munu (x) diag(sin theta) with
   sigma_munu typed out by hand (clover term, Sec. II-A);
 * gamma5-hermiticity of H, D and the even-odd operator, gauge covariance;
+* the gamma5-hermitian even-odd operator S_ee: exact gamma5-hermiticity,
+  S_ee = F_ee D^_ee, its source, and a dense solve on 4^4;
 * a dense brute-force matrix on a 2^4 lattice (every hop lands twice);
 * the clover inverse, the even-odd identities (Eqs. 5-9), dense LU solves
   against BiCGStab (Algs. 1-2), and finite differences for the gradient.
@@ -119,6 +121,8 @@ def test_free_field_plane_waves(dims, t_bc):
         got_e = oracle.dhat(dims, t_bc, U, Finv, kappa, pe)
         want = oracle.full_to_half(dims, 0, phase[:, None, None] * ((np.eye(4) - kappa**2 * Hp @ Hp) @ u)[None])
         assert rel(got_e, want) < 1e-14
+        # with F = 1 the gamma5-hermitian S_ee is the same operator
+        assert rel(oracle.schur_ee(dims, t_bc, U, F, Finv, kappa, pe), want) < 1e-14
 
 
 # ------------------------------------------------------------- P2, P3 clover
@@ -204,6 +208,33 @@ def test_gamma5_hermiticity(t_bc):
     lhs = vdot(xe, oracle.dhat(dims, t_bc, U, Fi, kappa, ye))
     w = oracle.site_apply(Fe, g5(oracle.dhat(dims, t_bc, U, Fi, kappa, g5(oracle.site_apply(Fie, xe)))))
     assert abs(lhs - vdot(w, ye)) / abs(lhs) < 1e-13
+
+
+@pytest.mark.parametrize("t_bc", [1, -1])
+def test_schur_operator_gamma5_hermitian_and_F_times_dhat(t_bc):
+    """S_ee = F_ee - k^2 H_eo F_oo^-1 H_oe: <x, S y> = <g5 S g5 x, y>
+    exactly (F commutes with g5, H^dag = g5 H g5), and S_ee = F_ee D^_ee,
+    D^_ee the operator of Eq. 8 pinned above (free field, dense solves).
+    The second identity fails if S applied F^-1 instead of F to p."""
+    dims = (4, 2, 4, 6)
+    kappa, csw = 0.124, 1.6
+    U = inputs.random_gauge(dims, 0.3, 16)
+    F = oracle.clover_field(dims, U, kappa, csw)
+    Fi = oracle.invert_sites(F)
+    Vh = inputs.volume(dims) // 2
+    xe = inputs.gaussian_source(dims, 17)[:Vh]
+    ye = inputs.gaussian_source(dims, 18)[:Vh]
+    g5 = lambda v: np.einsum("ab,sbi->sai", G5, v)
+    S = lambda v: oracle.schur_ee(dims, t_bc, U, F, Fi, kappa, v)
+    lhs = vdot(xe, S(ye))
+    assert abs(lhs - vdot(g5(S(g5(xe))), ye)) / abs(lhs) < 1e-14
+    assert abs(lhs - vdot(S(xe), ye)) / abs(lhs) > 1e-3  # not Hermitian itself: the check above has teeth
+    Fe = oracle.field_to_half(dims, 0, F)
+    assert rel(S(ye), oracle.site_apply(Fe, oracle.dhat(dims, t_bc, U, Fi, kappa, ye))) < 1e-14
+    # its source: with b = D x, S_ee x_e = b_e + k H_eo F_oo^-1 b_o
+    x = inputs.gaussian_source(dims, 19)
+    b = oracle.dirac(dims, t_bc, U, F, kappa, x)
+    assert rel(S(oracle.full_to_half(dims, 0, x)), oracle.schur_source(dims, t_bc, U, Fi, kappa, b)) < 1e-14
 
 
 # ------------------------------------------------------------- P5 covariance
@@ -330,6 +361,28 @@ def test_nested_bicgstab_matches_dense_solve(c1_problem):
     assert st == 0 and 1 <= outer <= 6 and inner > 0
     assert oracle.true_residual(P["dims"], P["t_bc"], P["U"], P["F"], P["kappa"], P["b"], x) <= 1e-12
     assert rel(x, P["xd"]) < 1e-10
+
+
+def test_schur_solve_matches_dense_solve(c1_problem):
+    """BiCGStab on S_ee against the dense LU solve of D, and the dense S_ee
+    (built column by column) against gamma5-hermiticity and its own solve."""
+    P = c1_problem
+    dims, t_bc, kappa = P["dims"], P["t_bc"], P["kappa"]
+    x, st, it = oracle.bicgstab_schur(dims, t_bc, P["U"], P["F"], P["Fi"], kappa, P["b"], 1e-13)
+    assert st == 0 and it > 5
+    assert oracle.true_residual(dims, t_bc, P["U"], P["F"], kappa, P["b"], x) <= 1e-12
+    assert rel(x, P["xd"]) < 1e-10
+    n = inputs.volume(dims) // 2 * 12
+    Sd = np.zeros((n, n), dtype=complex)
+    for k in range(n):
+        e = np.zeros(n, dtype=complex)
+        e[k] = 1
+        Sd[:, k] = oracle.schur_ee(dims, t_bc, P["U"], P["F"], P["Fi"], kappa, e.reshape(-1, 4, 3)).reshape(-1)
+    G5h = np.kron(np.eye(n // 12), np.kron(G5, np.eye(3)))
+    assert rel(Sd.conj().T, G5h @ Sd @ G5h) < 1e-14
+    src = oracle.schur_source(dims, t_bc, P["U"], P["Fi"], kappa, P["b"]).reshape(-1)
+    xe = np.linalg.solve(Sd, src).reshape(-1, 4, 3)
+    assert rel(xe, oracle.full_to_half(dims, 0, P["xd"])) < 1e-10
 
 
 # ------------------------------------------------------------- sampled sites
