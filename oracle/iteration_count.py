@@ -67,9 +67,10 @@ def main():
     by_host = data.get("by_host", {})
     by_host[platform.machine()] = out
     data["by_host"] = by_host
-    # the count the benchmark scales by; the iteration is the same on every
-    # host (IEEE FP64, no contraction, serial reductions), which the by_host
-    # entries record
+    # the count the benchmark scales by.  Each host's entry is kept: the
+    # links come from the host's LAPACK eigendecomposition and differ across
+    # hosts at the rounding level, so the residuals differ in their last
+    # digits; the iteration counts are what the by_host entries compare
     data["fp64_eo_24x24x24x48"] = out
     with open(args.out, "w") as f:
         json.dump(data, f, indent=1)
