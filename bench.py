@@ -478,6 +478,12 @@ def run_ours(args):
         o = qcd.default_opts(precision_levels=2, inner_tol=[W["inner_tol"], 1e-2], outer_df64=mode)
         t, info = timed_solves(torch, ctx, bd, x, W["tol"], o, 3)
         outer_modes[name] = solve_summary(t, info)
+    o = qcd.default_opts(precision_levels=2, inner_tol=[W["inner_tol"], 1e-2], eo_hermitian=1)
+    t, info = timed_solves(torch, ctx, bd, x, W["tol"], o, 3)
+    eo_forms = {"dhat_eq8": dict(solve_summary(ms_step * 1e-3, mixed), what="D^_ee = 1 - k^2 F_ee^-1 H_eo F_oo^-1 H_oe "
+                                 "(Eq. 8), the headline solve"),
+                "schur_ee": dict(solve_summary(t, info), what="gamma5-hermitian S_ee = F_ee D^_ee on every level, "
+                                 "same outer/inner precisions")}
     outer_modes["fp64_outer"]["what"] = "outer level all FP64 (Alg. 1 as printed), FP32 inner"
     outer_modes["df64_outer"]["what"] = ("outer level all DF64, x_e, b^_e and x_o included (FP64 dots, norms and "
                                          "true residual), FP32 inner")
@@ -569,6 +575,7 @@ def run_ours(args):
                   "dhat_applies": mixed["dhat_applies"], "true_resid": mixed["true_resid"],
                   "restarts": mixed["restarts"]},
         "outer_modes": outer_modes,
+        "eo_operator": eo_forms,
         "fp64_only": {"seconds": round(fp64_s, 6), "iterations": info64["outer_iters"],
                       "dhat_applies": info64["dhat_applies"][0], "true_resid": info64["true_resid"]},
         "speedup_vs_fp64": round(fp64_s / (ms_step * 1e-3), 3),

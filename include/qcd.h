@@ -150,6 +150,13 @@ int qcd_mult_eo(qcd_ctx *ctx, void *out, const void *in, int out_parity, int dag
  * vectors.  Same buffer conventions (nrhs right-hand sides). */
 int qcd_dhat(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
 
+/* out = S_ee in = F_ee in - kappa^2 H_eo F_oo^-1 H_oe in, the Schur
+ * complement of D on the even sites (Sec. II-B, Eqs. 5-8: D^_ee of Eq. 8 is
+ * F_ee^-1 S_ee), which unlike D^_ee is gamma5-hermitian: S_ee^dag =
+ * gamma5 S_ee gamma5.  Even half vectors, same buffer conventions as
+ * qcd_dhat (nrhs right-hand sides).  Needs qcd_clover_build. */
+int qcd_schur_ee(qcd_ctx *ctx, void *out, const void *in, int prec, int nrhs);
+
 /* out = D in = F in - kappa H in on the full lattice (Eq. 3), FP64,
  * canonical complex128 [V][4][3] device buffers. */
 int qcd_dirac(qcd_ctx *ctx, void *out, const void *in);
@@ -178,6 +185,15 @@ typedef struct {
                              Outer dot products and norms are summed in FP64
                              and the final true residual is FP64 in every
                              mode; QCD_EINVAL outside 0..2 */
+    int eo_hermitian;     /* even_odd = 1: 0 (default) iterates on
+                             D^_ee = 1 - kappa^2 F_ee^-1 H_eo F_oo^-1 H_oe
+                             (Eq. 8); 1 on the gamma5-hermitian Schur
+                             complement S_ee = F_ee D^_ee = F_ee - kappa^2
+                             H_eo F_oo^-1 H_oe with right-hand side
+                             b_e + kappa H_eo F_oo^-1 b_o (its residual is the
+                             even part of b - D x itself); x_o as Eq. 7.
+                             Every level uses the chosen operator.  Not
+                             available to qcd_solve_batched (QCD_EINVAL) */
 } qcd_solve_opts;
 
 typedef struct {
@@ -192,7 +208,7 @@ typedef struct {
 
 /* Defaults: precision_levels 2, even_odd 1, inner_tol {1e-5, 1e-2},
  * max_outer 200, max_inner {250, 250}, max_restarts 5, use_x0 0,
- * outer_df64 1. */
+ * outer_df64 1, eo_hermitian 0. */
 void qcd_solve_opts_default(qcd_solve_opts *opts);
 
 /* Solve D x = b to ||b - D x|| / ||b|| <= tol (recomputed in FP64 at exit;

@@ -386,14 +386,14 @@ int op_half(qcd_ctx *c, void *out, const void *in, int prec, int nrhs, int kind,
             s.rhs_stride = B.stride;
             s.norm_stride = (size_t)c->g.Vh_pad;
             s.dagger = dagger;
-            if (kind == 2) {  // D^ = 1 - kappa^2 H~_eo H~_oe
+            if (kind == 2 || kind == 4) {  // D^ = 1 - kappa^2 H~_eo H~_oe, or S_ee = F_ee D^
                 s.mode = M_MULT;
                 s.out_par = 1;
                 s.out = B.tmp;
                 s.in = B.in;
                 rc = launch_stencil(c, s);
                 if (rc) return rc;
-                s.mode = M_DHAT;
+                s.mode = kind == 4 ? M_FULL : M_DHAT;
                 s.out_par = 0;
                 s.out = B.out;
                 s.in = B.tmp;
@@ -438,6 +438,13 @@ extern "C" int qcd_dhat(qcd_ctx *c, void *out, const void *in, int prec, int nrh
     int rc = check_op_args(c, out, in, prec, nrhs, true);
     if (rc) return rc;
     return op_half(c, out, in, prec, nrhs, 2, 0, 0, 0);
+}
+
+extern "C" int qcd_schur_ee(qcd_ctx *c, void *out, const void *in, int prec, int nrhs)
+{
+    int rc = check_op_args(c, out, in, prec, nrhs, true);
+    if (rc) return rc;
+    return op_half(c, out, in, prec, nrhs, 4, 0, 0, 0);
 }
 
 extern "C" int qcd_clover_apply(qcd_ctx *c, void *out, const void *in, int parity, int inverse, int prec, int nrhs)
@@ -490,6 +497,7 @@ extern "C" void qcd_solve_opts_default(qcd_solve_opts *o)
     o->max_restarts = 5;
     o->use_x0 = 0;
     o->outer_df64 = 1;
+    o->eo_hermitian = 0;
 }
 
 extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const qcd_solve_opts *opts,
@@ -504,7 +512,8 @@ extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const q
     if (opts) o = *opts;
     if (o.precision_levels < 1 || o.precision_levels > 3 || (!o.even_odd && o.precision_levels != 1) ||
         !(tol > 0.0) || o.max_outer < 1 || o.max_inner[0] < 1 || o.max_inner[1] < 1 || o.max_restarts < 0 ||
-        !(o.inner_tol[0] > 0.0) || !(o.inner_tol[1] > 0.0) || o.outer_df64 < 0 || o.outer_df64 > 2) {
+        !(o.inner_tol[0] > 0.0) || !(o.inner_tol[1] > 0.0) || o.outer_df64 < 0 || o.outer_df64 > 2 ||
+        o.eo_hermitian < 0 || o.eo_hermitian > 1) {
         set_error_message("invalid solver options");
         return QCD_EINVAL;
     }
@@ -585,7 +594,7 @@ extern "C" int qcd_solve_batched(qcd_ctx *const *ctxs, int n, const void *const 
     qcd_solve_opts_default(&o);
     if (opts) o = *opts;
     if (o.precision_levels != 2 || !o.even_odd || o.use_x0 || o.max_outer < 1 || o.max_inner[0] < 1 ||
-        !(o.inner_tol[0] > 0.0) || o.outer_df64 < 0 || o.outer_df64 > 2) {
+        !(o.inner_tol[0] > 0.0) || o.outer_df64 < 0 || o.outer_df64 > 2 || o.eo_hermitian != 0) {
         set_error_message("batched solves run the even-odd FP64/FP32 scheme from x = 0");
         return QCD_EINVAL;
     }

@@ -26,6 +26,7 @@ constexpr double BD_EPS_LOW = 1e-12;
 
 struct Level {
     int prec = QCD_F64;
+    int form = 0;                    // 0: D^_ee (Eq. 8); 1: S_ee = F_ee D^_ee (gamma5-hermitian)
     HVec x, r, rt, p, q, t, v, tmp;  // tmp: odd-parity workspace of D^
     SolverState *st = nullptr;       // device
     int slot = 0;                    // index into the state arrays
@@ -46,10 +47,11 @@ int read_state(qcd_ctx *c, int slot, SolverState *out)
         if (rc__ != QCD_OK) return rc__; \
     } while (0)
 
-// out = D^ in = in - kappa^2 F_ee^-1 H_eo F_oo^-1 H_oe in (Eq. 8) with a
-// reduction fused into the second half.
+// out = D^ in = in - kappa^2 F_ee^-1 H_eo F_oo^-1 H_oe in (Eq. 8), or for
+// form 1 the gamma5-hermitian S_ee in = F_ee in - kappa^2 H_eo F_oo^-1 H_oe in,
+// with a reduction fused into the second half.
 int dhat(qcd_ctx *c, int prec, HVec in, HVec out, HVec tmp, int red, HVec aux, SolverState *st, int fin,
-         const int *done)
+         const int *done, int form)
 {
     StencilCall s1;
     s1.prec = prec;
@@ -61,7 +63,7 @@ int dhat(qcd_ctx *c, int prec, HVec in, HVec out, HVec tmp, int red, HVec aux, S
     TRY(launch_stencil(c, s1));
     StencilCall s2;
     s2.prec = prec;
-    s2.mode = M_DHAT;
+    s2.mode = form ? M_FULL : M_DHAT;  // F_ee in (M_FULL) or in (M_DHAT), minus kappa^2 [F_ee^-1] H_eo tmp
     s2.out_par = 0;
     s2.out = out;
     s2.in = tmp;
@@ -83,9 +85,9 @@ int bicg_iteration(qcd_ctx *c, Level &L)
 {
     const int n = c->g.Vh_pad;
     const int *done = &L.st->done;
-    TRY(dhat(c, L.prec, L.p, L.q, L.tmp, R_DOT_AUX, L.rt, L.st, FIN_ALPHA, done));  // q = D^ p, alpha
+    TRY(dhat(c, L.prec, L.p, L.q, L.tmp, R_DOT_AUX, L.rt, L.st, FIN_ALPHA, done, L.form));  // q = D^ p, alpha
     TRY(blas_update_s(c, L.prec, n, L.r, L.q, L.st));                              // s = r - alpha q
-    TRY(dhat(c, L.prec, L.r, L.t, L.tmp, R_OMEGA, L.r, L.st, FIN_OMEGA, done));     // t = D^ s, omega
+    TRY(dhat(c, L.prec, L.r, L.t, L.tmp, R_OMEGA, L.r, L.st, FIN_OMEGA, done, L.form));     // t = D^ s, omega
     TRY(blas_update_x(c, L.prec, n, L.x, L.p, L.r, L.t, L.rt, L.st));              // x, r, beta
     TRY(blas_update_p(c, L.prec, n, L.p, L.r, L.q, L.st, FIN_NONE));               // p
     return QCD_OK;
@@ -145,9 +147,10 @@ struct Solver {
     SolverState *aux;
 };
 
-int get_level(qcd_ctx *c, Level &L, int prec, int first_slot, int state_slot)
+int get_level(qcd_ctx *c, Level &L, int prec, int first_slot, int state_slot, int form)
 {
     L.prec = prec;
+    L.form = form;
     HVec *v[8] = {&L.x, &L.r, &L.rt, &L.p, &L.q, &L.t, &L.v, &L.tmp};
     for (int k = 0; k < 8; ++k) TRY(get_work(c, prec, first_slot + k, v[k]));
     L.slot = state_slot;
@@ -172,13 +175,13 @@ int flexible(Solver &S, int lev)
     if (h.done) return QCD_OK;
     for (;;) {
         TRY(precondition(S, lev + 1, L.p, L.prec, &L.st->norm2[1], L.v, done));      // v = M p
-        TRY(dhat(c, L.prec, L.v, L.q, L.tmp, R_DOT_AUX, L.rt, L.st, FIN_ALPHA, done));  // q = D^ v, alpha
+        TRY(dhat(c, L.prec, L.v, L.q, L.tmp, R_DOT_AUX, L.rt, L.st, FIN_ALPHA, done, L.form));  // q = D^ v, alpha
         TRY(blas_flex1(c, L.prec, n, L.x, L.v, L.r, L.q, L.st));                       // x, r, |r|
         S.info.dhat_applies[L.prec == QCD_DF64 ? QCD_F64 : L.prec] += 1;  // DF64 counts as the FP64 level
         TRY(read_state(c, L.slot, &h));
         if (h.done) break;
         TRY(precondition(S, lev + 1, L.r, L.prec, &L.st->rr, L.v, done));                // v = M r
-        TRY(dhat(c, L.prec, L.v, L.t, L.tmp, R_OMEGA, L.r, L.st, FIN_OMEGA, done));      // t = D^ v, omega
+        TRY(dhat(c, L.prec, L.v, L.t, L.tmp, R_OMEGA, L.r, L.st, FIN_OMEGA, done, L.form));      // t = D^ v, omega
         TRY(blas_flex2(c, L.prec, n, L.x, L.v, L.r, L.t, L.rt, L.st));                  // x, r, beta
         TRY(blas_update_p(c, L.prec, n, L.p, L.r, L.q, L.st, FIN_SETN + 1));             // p, |p|
         S.info.dhat_applies[L.prec == QCD_DF64 ? QCD_F64 : L.prec] += 1;
@@ -214,8 +217,9 @@ int precondition(Solver &S, int level, HVec src, int src_prec, const double *src
 
 int residual_eo(Solver &S, HVec xe, HVec out, SolverState *st, int fin)
 {
-    // out = b^ - D^ x_e = b^ - x_e + kappa^2 H~_eo H~_oe x_e, in the outer
-    // level's arithmetic
+    // out = b^ - D^ x_e = b^ - x_e + kappa^2 H~_eo H~_oe x_e (or for the
+    // gamma5-hermitian form src - F_ee x_e + kappa^2 H_eo F_oo^-1 H_oe x_e),
+    // in the outer level's arithmetic
     qcd_ctx *c = S.c;
     Level &L = S.lv[0];
     StencilCall s1;
@@ -227,7 +231,7 @@ int residual_eo(Solver &S, HVec xe, HVec out, SolverState *st, int fin)
     TRY(launch_stencil(c, s1));
     StencilCall s2;
     s2.prec = L.prec;
-    s2.mode = M_DHAT;
+    s2.mode = L.form ? M_FULL : M_DHAT;
     s2.out_par = 0;
     s2.out = out;
     s2.in = L.tmp;
@@ -302,6 +306,11 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     // mode, and the true-residual check ||b - D x|| that decides convergence
     // is FP64 from the FP64 links and clover term.
     const int mode = S.o.precision_levels >= 2 ? S.o.outer_df64 : 0;
+    // the even-odd operator: D^_ee of Eq. 8 (form 0) or the gamma5-hermitian
+    // S_ee = F_ee D^_ee (form 1), whose right-hand side is F_ee b^_e =
+    // b_e + kappa H_eo F_oo^-1 b_o and whose residual is the even part of the
+    // full residual itself
+    const int form = S.o.eo_hermitian ? 1 : 0;
     const int P0 = mode ? QCD_DF64 : QCD_F64;
     const int PX = mode == 2 ? QCD_DF64 : QCD_F64;
     TRY(get_work(c, QCD_F64, 0, &S.be));
@@ -310,7 +319,7 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
     TRY(get_work(c, QCD_F64, 4, &S.re));
     TRY(get_work(c, QCD_F64, 5, &S.ro));
     TRY(get_work(c, PX, 2, &S.bhat));
-    TRY(get_level(c, O, P0, 6, ST_OUTER));
+    TRY(get_level(c, O, P0, 6, ST_OUTER, form));
     HVec beX = S.be, boX = S.bo, xoX = S.xo, xe64 = O.x, xe0 = O.x, tmpX = O.tmp;
     S.bhat0 = S.bhat;
     if (PX != QCD_F64) {  // all-DF64 outer level: DF64 copies of b_e, b_o, x_o
@@ -325,8 +334,8 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         TRY(get_work(c, P0, 2, &S.bhat0));   // b^_e rounded to DF64
         tmpX = S.re;                          // FP64 scratch before the true residual needs it
     }
-    if (S.o.precision_levels >= 2) TRY(get_level(c, S.lv[1], QCD_F32, 0, ST_MID));
-    if (S.o.precision_levels >= 3) TRY(get_level(c, S.lv[2], QCD_F16, 0, ST_INNER));
+    if (S.o.precision_levels >= 2) TRY(get_level(c, S.lv[1], QCD_F32, 0, ST_MID, form));
+    if (S.o.precision_levels >= 3) TRY(get_level(c, S.lv[2], QCD_F16, 0, ST_INNER, form));
     S.aux = c->states + ST_AUX;
 
     // b -> (b_e, b_o); |b|^2
@@ -339,18 +348,26 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         TRY(convert_half(c, S.be, beX));
         TRY(convert_half(c, S.bo, boX));
     }
-    // b^_e = F_ee^-1 (b_e + kappa H_eo F_oo^-1 b_o)   (Eq. 6, Alg. 1 line 3)
+    // b^_e = F_ee^-1 (b_e + kappa H_eo F_oo^-1 b_o)   (Eq. 6, Alg. 1 line 3),
+    // for form 1 without the left F_ee^-1
     TRY(clover_apply_half(c, PX, 1, 1, boX, tmpX, 1, 0));
     {
         StencilCall s;
         s.prec = PX;
-        s.mode = M_SRC;
         s.out_par = 0;
         s.out = S.bhat;
         s.in = tmpX;
         s.y = beX;
-        s.a = 1.0;
         s.cc = c->kappa;
+        if (form) {  // 0 F_ee b_e + kappa H_eo tmp + b_e
+            s.mode = M_FULL;
+            s.a = 0.0;
+            s.z = beX;
+            s.d = 1.0;
+        } else {
+            s.mode = M_SRC;
+            s.a = 1.0;
+        }
         TRY(launch_stencil(c, s));
     }
     if (PX != P0) TRY(convert_half(c, S.bhat, S.bhat0));

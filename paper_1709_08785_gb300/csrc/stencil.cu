@@ -132,7 +132,10 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
         set_error_message("reduction grid too large");
         return QCD_EINVAL;
     }
-    const int cls = p == QCD_F32    ? (sc.mode == M_DHAT ? QCD_K_DHAT_F32 : QCD_K_MULT_F32)
+    // the second half of an even-odd operator with its fused dots (D^_ee:
+    // M_DHAT; S_ee: M_FULL with a reduction) is timed apart from the MULTs
+    const bool second_half = sc.mode == M_DHAT || (sc.mode == M_FULL && sc.red != R_NONE);
+    const int cls = p == QCD_F32    ? (second_half ? QCD_K_DHAT_F32 : QCD_K_MULT_F32)
                     : p == QCD_F16  ? QCD_K_MULT_F16
                     : p == QCD_DF64 ? QCD_K_MULT_DF64
                                     : QCD_K_MULT_F64;

@@ -20,6 +20,25 @@
 
 namespace qcd {
 
+// <o|v> and |o|^2 of one site into red[0..2] (the omega of Alg. 2)
+template <class T, class RA>
+__device__ __forceinline__ void omega_sums(const Spinor<T> &o_, const Spinor<T> &v_, RA red[4])
+{
+    T dr = 0, di = 0, nn = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const cx<T> o = o_.s[s][i], v = v_.s[s][i];
+            dr += o.r * v.r + o.i * v.i;
+            di += o.r * v.i - o.i * v.r;
+            nn += o.r * o.r + o.i * o.i;
+        }
+    red[0] += acc_cast<RA>(dr);
+    red[1] += acc_cast<RA>(di);
+    red[2] += acc_cast<RA>(nn);
+}
+
 // One output site cb (right-hand side r): the hops, the mode's epilogue, the
 // site's contributions to the fused reductions.
 template <int P, int MODE, int RED, bool DAG, class RA>
@@ -44,19 +63,7 @@ __device__ __forceinline__ void stencil_site(const StencilArgs &A, int cb, int r
         }
         if (RED == R_OMEGA) {  // <out|aux>, |out|^2 (aux is usually y)
             if (A.aux.p != A.y.p) Prec<P>::load(rhs_ptr(A.aux, r, A.rhs_stride, A.norm_stride), cb, y);
-            T dr = 0, di = 0, nn = 0;
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const cx<T> o = acc.s[s][i], v = y.s[s][i];
-                    dr += o.r * v.r + o.i * v.i;
-                    di += o.r * v.i - o.i * v.r;
-                    nn += o.r * o.r + o.i * o.i;
-                }
-            red[0] += acc_cast<RA>(dr);
-            red[1] += acc_cast<RA>(di);
-            red[2] += acc_cast<RA>(nn);
+            omega_sums<T, RA>(acc, y, red);
         }
     } else if (MODE == M_SRC) {
         Spinor<T> y;
@@ -64,14 +71,21 @@ __device__ __forceinline__ void stencil_site(const StencilArgs &A, int cb, int r
         axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
         clover_any<P>(A.C,A.out_par, cb, acc);
     } else if (MODE == M_FULL) {
+        // also the second half of the gamma5-hermitian S_ee = F_ee - k^2 H_eo F_oo^-1 H_oe
+        // (a = 1, cc = -k^2, y = the operator's input), with its dot products
         Spinor<T> y;
         Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
-        clover_any<P>(A.C,A.out_par, cb, y);
-        axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
+        Spinor<T> fy = y;
+        clover_any<P>(A.C,A.out_par, cb, fy);
+        axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), fy);
         if (A.has_z) {
             Spinor<T> z;
             Prec<P>::load(rhs_ptr(A.z, r, A.rhs_stride, A.norm_stride), cb, z);
             axpby_sp(acc, T(1), acc, sarg<T>(A.d, A.df32), z);
+        }
+        if (RED == R_OMEGA) {  // <out|aux>, |out|^2 (aux is usually y)
+            if (A.aux.p != A.y.p) Prec<P>::load(rhs_ptr(A.aux, r, A.rhs_stride, A.norm_stride), cb, y);
+            omega_sums<T, RA>(acc, y, red);
         }
     }
     if (RED == R_DOT_AUX) {  // <aux|out>
@@ -190,6 +204,8 @@ int dispatch(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block,
     QCD_CASE(M_SRC, R_NORM)
     QCD_CASE(M_FULL, R_NONE)
     QCD_CASE(M_FULL, R_NORM)
+    QCD_CASE(M_FULL, R_DOT_AUX)
+    QCD_CASE(M_FULL, R_OMEGA)
 #undef QCD_CASE
     set_error_message("unsupported stencil mode %d / reduction %d", sc.mode, sc.red);
     return QCD_EINVAL;

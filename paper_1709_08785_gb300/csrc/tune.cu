@@ -187,6 +187,11 @@ int autotune(qcd_ctx *c, const char *cache_path)
         {QCD_F16, M_MULT, R_NONE, 12},
         {QCD_DF64, M_MULT, R_NONE, 1}, {QCD_DF64, M_DHAT, R_DOT_AUX, 1}, {QCD_DF64, M_DHAT, R_OMEGA, 1},
         {QCD_DF64, M_SRC, R_NONE, 1},  {QCD_DF64, M_DHAT, R_NORM, 1},
+        // the second halves of the gamma5-hermitian S_ee
+        {QCD_F64, M_FULL, R_DOT_AUX, 1}, {QCD_F64, M_FULL, R_OMEGA, 1},
+        {QCD_F32, M_FULL, R_DOT_AUX, 1}, {QCD_F32, M_FULL, R_OMEGA, 1},
+        {QCD_F16, M_FULL, R_DOT_AUX, 1}, {QCD_F16, M_FULL, R_OMEGA, 1},
+        {QCD_DF64, M_FULL, R_DOT_AUX, 1}, {QCD_DF64, M_FULL, R_OMEGA, 1}, {QCD_DF64, M_FULL, R_NORM, 1},
     };
     Cache cache = read_cache(cache_path);
     const std::string prefix = cache_prefix(c);

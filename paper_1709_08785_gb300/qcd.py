@@ -38,6 +38,7 @@ class SolveOpts(ctypes.Structure):
         ("max_restarts", ctypes.c_int),
         ("use_x0", ctypes.c_int),
         ("outer_df64", ctypes.c_int),
+        ("eo_hermitian", ctypes.c_int),
     ]
 
 
@@ -68,7 +69,7 @@ EXPORTS = [
     "qcd_set_profiling", "qcd_kernel_stats", "qcd_reset_kernel_stats", "qcd_strerror", "qcd_last_error",
     "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_mult_throughput", "qcd_dslash_eo_noalloc",
     "qcd_solve_adjoint", "qcd_force", "qcd_autotune", "qcd_tune_info", "qcd_solve_batched", "qcd_set_wait_limit",
-    "qcd_set_graphs", "qcd_pion_correlator",
+    "qcd_set_graphs", "qcd_pion_correlator", "qcd_schur_ee",
 ]
 
 _lib = None
@@ -102,6 +103,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.qcd_clover_apply.argtypes = [vp, vp, vp, ip, ip, ip, ip]
     lib.qcd_mult_eo.argtypes = [vp, vp, vp, ip, ip, ip, ip]
     lib.qcd_dhat.argtypes = [vp, vp, vp, ip, ip]
+    lib.qcd_schur_ee.argtypes = [vp, vp, vp, ip, ip]
     lib.qcd_dirac.argtypes = [vp, vp, vp]
     lib.qcd_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
     lib.qcd_solve_opts_default.restype = None
@@ -254,6 +256,10 @@ class Context:
 
     def dhat(self, out, inp, prec: int = F64, nrhs: int = 1):
         _check(self.lib.qcd_dhat(self._h, _ptr(out), _ptr(inp), int(prec), int(nrhs)))
+
+    def schur_ee(self, out, inp, prec: int = F64, nrhs: int = 1):
+        """out = S_ee inp = F_ee inp - kappa^2 H_eo F_oo^-1 H_oe inp (even half vectors)."""
+        _check(self.lib.qcd_schur_ee(self._h, _ptr(out), _ptr(inp), int(prec), int(nrhs)))
 
     def dirac(self, out, inp):
         _check(self.lib.qcd_dirac(self._h, _ptr(out), _ptr(inp)))

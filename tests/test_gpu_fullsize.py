@@ -81,12 +81,15 @@ def test_24c48_dirac_sampled(lat24):
     assert rel(out.cpu().numpy()[sites], want) < 1e-13
 
 
-def test_24c48_mixed_solve_true_residual(lat24):
+@pytest.mark.parametrize("eo_hermitian", [0, 1])
+def test_24c48_mixed_solve_true_residual(lat24, eo_hermitian):
     bd = torch.from_numpy(lat24["b"]).cuda()
     x = torch.zeros_like(bd)
-    info = lat24["ctx"].solve(bd, x, tol=1e-12, precision_levels=2)
+    info = lat24["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, eo_hermitian=eo_hermitian)
     assert info["status"] == 0 and info["true_resid"] <= 1e-12
-    F = oracle.clover_field(lat24["dims"], lat24["U"], lat24["kappa"], lat24["csw"])
+    if "F" not in lat24:  # the oracle's clover field, built once for both forms
+        lat24["F"] = oracle.clover_field(lat24["dims"], lat24["U"], lat24["kappa"], lat24["csw"])
+    F = lat24["F"]
     r = oracle.true_residual(lat24["dims"], lat24["t_bc"], lat24["U"], F, lat24["kappa"], lat24["b"], x.cpu().numpy())
     assert r <= 1e-12, r
     # the solver's FP64 true residual against the oracle's

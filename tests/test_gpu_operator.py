@@ -103,6 +103,21 @@ def test_dhat(lat, prec):
     assert rel(got, want) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_schur_ee(lat, prec, nrhs):
+    """The gamma5-hermitian even-odd operator S_ee = F_ee - k^2 H_eo F_oo^-1 H_oe
+    (second half with the clover term F, not its inverse)."""
+    dims = lat["dims"]
+    Vh = inputs.volume(dims) // 2
+    vs = np.stack([inputs.gaussian_source(dims, 56 + k)[:Vh] for k in range(nrhs)])
+    got = run(lambda o, i, p, n: lat["ctx"].schur_ee(o, i, p, n), vs if nrhs > 1 else vs[0], prec, nrhs)
+    got = got.reshape(nrhs, Vh, 4, 3)
+    for k in range(nrhs):
+        want = oracle.schur_ee(dims, lat["t_bc"], lat["U"], lat["F"], lat["Fi"], lat["kappa"], vs[k])
+        assert rel(got[k], want) < TOL[prec]
+
+
 def test_dirac_full(lat):
     dims = lat["dims"]
     v = inputs.gaussian_source(dims, 54)

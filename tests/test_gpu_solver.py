@@ -150,6 +150,31 @@ def test_solution_storage_is_fp64(lat8, mode):
     assert np.linalg.norm(xs[~ev] - x0[~ev]) / np.linalg.norm(x0[~ev]) < 1e-13
 
 
+@pytest.mark.parametrize("levels", [1, 2, 3])
+@pytest.mark.parametrize("lat", ["lat4", "lat8"])
+def test_gamma5_hermitian_form_solves(request, lat, levels):
+    """Every level iterating on the gamma5-hermitian S_ee = F_ee D^_ee
+    (eo_hermitian = 1): the oracle's true residual meets 1e-12 and the
+    solution agrees with the oracle's own BiCGStab on S_ee."""
+    P = request.getfixturevalue(lat)
+    x, info = solve(P, precision_levels=levels, eo_hermitian=1)
+    assert info["status"] == 0, info
+    r = true_res(P, x)
+    assert r <= 1e-12, (r, info)
+    assert abs(info["true_resid"] - r) <= 5e-15, (info["true_resid"], r)
+    Fi = oracle.invert_sites(P["F"])
+    xo, st, _ = oracle.bicgstab_schur(P["dims"], P["t_bc"], P["U"], P["F"], Fi, P["kappa"], P["b"], 1e-13)
+    assert st == 0
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-10
+
+
+def test_gamma5_hermitian_form_rejected_by_batched(lat4):
+    qcd = lat4["qcd"]
+    bd = torch.from_numpy(lat4["b"]).cuda()
+    with pytest.raises(qcd.QCDError):
+        qcd.solve_batched([lat4["ctx"]], [bd], [torch.zeros_like(bd)], [1e-10], precision_levels=2, eo_hermitian=1)
+
+
 def test_host_buffers(lat4):
     x = np.zeros_like(lat4["b"])
     info = lat4["ctx"].solve(lat4["b"], x, tol=1e-12, precision_levels=2)
@@ -233,6 +258,10 @@ def test_invalid_arguments(lat4):
         lat4["ctx"].solve(bd, x, tol=-1.0)
     with pytest.raises(qcd.QCDError):
         lat4["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, even_odd=0)
+    with pytest.raises(qcd.QCDError):  # outer_df64 outside 0..2
+        lat4["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, outer_df64=3)
+    with pytest.raises(qcd.QCDError):
+        lat4["ctx"].solve(bd, x, tol=1e-12, precision_levels=2, eo_hermitian=2)
     with pytest.raises(qcd.QCDError):
         qcd.Context((4, 4, 3, 4))
     ctx = qcd.Context((4, 4, 4, 4))
