@@ -634,9 +634,13 @@ def run_dslash_only(args):
     out = {"mode": "dslash-only", "lattice": list(dims), "peak_gbs": hbm, "peak_kind": kind}
     for name, p, nrhs in (("f32", qcd.F32, 1), ("f16", qcd.F16, 1), ("f64", qcd.F64, 1), ("df64", qcd.DF64, 1),
                           ("f32_12rhs", qcd.F32, 12)):
+        # one NVTX range per precision, so that a profiler can select it
+        torch.cuda.nvtx.range_push("dslash_" + name)
         r = ctx.mult_benchmark(p, nrhs, max(3, args.steps))
+        torch.cuda.nvtx.range_pop()
         out[name] = {"gbs": round(r["gbs"], 1), "frac_hbm": round(r["gbs"] / hbm, 3), "us": round(r["ms"] * 1e3, 2),
                      "bytes": r["bytes"]}
+    out["tuned"] = [t for t in ctx.tune_info() if t["mode"] in (1, 2, 4) and t["nrhs"] in (1, 12)]
     print(json.dumps(out))
     ctx.close()
     return 0

@@ -314,8 +314,11 @@ long qcd_launch_count(const qcd_ctx *ctx);
  * Synchronous. */
 int qcd_autotune(qcd_ctx *ctx, const char *cache_path);
 
-/* The tuned configurations: up to max entries (key; variant, 1 for the
- * capped register budget; threads per block along the sites, or
+/* The tuned configurations: up to max entries (key; variant: 0 the
+ * compiler's register budget, 1 capped at 80 registers (128 for QCD_DF64),
+ * 2 the FP32 / FP16 kernel whose hops are software-pipelined (the next
+ * hop's neighbour spinor and link loaded before the current hop computes);
+ * threads per block along the sites, or
  * right-hand sides per block for the multi-RHS kernel; microseconds per
  * launch); returns the number of entries held. Any output pointer may be
  * NULL. */

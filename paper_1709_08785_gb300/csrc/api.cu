@@ -722,20 +722,6 @@ extern "C" int qcd_tune_info(qcd_ctx *c, int max, unsigned *keys, int *variant, 
 
 namespace {
 
-// Reads every line of the flush buffer once (clean lines replace whatever L2
-// held; dirty lines of earlier kernels are written back here, not inside the
-// timed launch).  The sink is written only if the sum equals a value the
-// buffer never produces, which keeps the loads.
-__global__ void k_l2_evict(const uint4 *__restrict__ buf, size_t n, unsigned *sink)
-{
-    unsigned acc = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const uint4 v = __ldcs(buf + i);
-        acc += v.x ^ v.y ^ v.z ^ v.w;
-    }
-    if (acc == 0x9e3779b9u) *sink = acc;
-}
-
 // The benchmark buffers: nrhs input and output vectors in precision prec,
 // the input filled with a fixed pattern.
 int bench_buffers(qcd_ctx *c, int prec, int nrhs, StencilCall &s)
@@ -798,20 +784,12 @@ extern "C" int qcd_mult_benchmark(qcd_ctx *c, int prec, int nrhs, int iters, dou
     if ((rc = bench_check(c, prec, nrhs, iters, ms_per_launch, bytes_per_launch))) return rc;
     StencilCall s;
     if ((rc = bench_buffers(c, prec, nrhs, s))) return rc;
-    const size_t flush_bytes = 256u << 20;
-    if (!c->flush_buf) {
-        if ((rc = dev_alloc(c, &c->flush_buf, flush_bytes + 256))) return rc;
-        QCD_CUDA_CHECK(cudaMemsetAsync(c->flush_buf, 0x5a, flush_bytes + 256, c->stream));
-    }
-    const uint4 *fb = (const uint4 *)c->flush_buf;
-    unsigned *sink = (unsigned *)((char *)c->flush_buf + flush_bytes);
     cudaEvent_t e0, e1;
     QCD_CUDA_CHECK(cudaEventCreate(&e0));
     QCD_CUDA_CHECK(cudaEventCreate(&e1));
     double total = 0.0;
     for (int it = -2; it < iters; ++it) {  // two untimed warm-up launches
-        k_l2_evict<<<c->num_sms * 8, 256, 0, c->stream>>>(fb, flush_bytes / sizeof(uint4), sink);
-        QCD_CUDA_CHECK(cudaGetLastError());
+        if ((rc = l2_evict(c))) break;
         QCD_CUDA_CHECK(cudaEventRecord(e0, c->stream));
         if ((rc = launch_stencil(c, s))) break;
         QCD_CUDA_CHECK(cudaEventRecord(e1, c->stream));

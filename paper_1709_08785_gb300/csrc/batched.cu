@@ -691,19 +691,26 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
             c->stream = keep;
             return r;
         }
+        // (with an FP64 solution the reconstruction pass also yields the odd
+        // rows of the true residual, as in the single solve)
         StencilCall sx;
         sx.prec = PX;
-        sx.mode = M_SRC;
+        sx.mode = PX == QCD_F64 ? M_RECON : M_SRC;
         sx.out_par = 1;
         sx.out = xoX;
         sx.in = XX;
         sx.y = boX;
         sx.a = 1.0;
         sx.cc = c->kappa;
+        if (PX == QCD_F64) {
+            sx.red = R_NORM;
+            sx.red_args = RedArgs{c->partials, c->counters, c->states + ST_AUX, FIN_SETN + 2};
+        }
         r = launch_stencil(c, sx);
         if (!r && PX != QCD_F64) r = convert_half(c, XX, X);
         if (!r && PX != QCD_F64) r = convert_half(c, xoX, xo);
-        for (int par = 0; par < 2 && !r; ++par) {
+        const int npar = PX == QCD_F64 ? 1 : 2;  // the even rows (and the odd ones unless fused above)
+        for (int par = 0; par < npar && !r; ++par) {
             StencilCall sr;
             sr.prec = QCD_F64;
             sr.mode = M_FULL;
@@ -716,7 +723,8 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
             sr.z = par ? bo : be;
             sr.d = 1.0;
             sr.red = R_NORM;
-            sr.red_args = RedArgs{c->partials, c->counters, c->states + ST_AUX, par ? FIN_ADDN + 2 : FIN_SETN + 2};
+            sr.red_args = RedArgs{c->partials, c->counters, c->states + ST_AUX,
+                                  (par || PX == QCD_F64) ? FIN_ADDN + 2 : FIN_SETN + 2};
             r = launch_stencil(c, sr);
         }
         if (!r) r = half_to_canon(c, QCD_F64, 0, X, x[i], 0, 1, 0);

@@ -83,7 +83,7 @@ struct RedArgs {
     int op = FIN_NONE;
 };
 
-enum StencilMode { M_HOP = 0, M_MULT = 1, M_DHAT = 2, M_SRC = 3, M_FULL = 4 };
+enum StencilMode { M_HOP = 0, M_MULT = 1, M_DHAT = 2, M_SRC = 3, M_FULL = 4, M_RECON = 5 };
 enum StencilRed { R_NONE = 0, R_DOT_AUX = 1, R_OMEGA = 2, R_NORM = 3 };
 
 }  // namespace qcd
@@ -157,7 +157,7 @@ struct qcd_ctx {
 
     // autotuned launch configurations of the stencil kernels, by tune_key
     struct TuneEntry {
-        int variant;  // 0: compiler's register budget, 1: capped at 80
+        int variant;  // 0: compiler's register budget; 1: capped at 80 (DF64: 128); 2: pipelined hops
         int bx;       // threads per block along the sites
         double us;    // measured time of one launch
     };
@@ -237,6 +237,7 @@ int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, c
 
 // tune.cu
 int autotune(qcd_ctx *c, const char *cache_path);
+int l2_evict(qcd_ctx *c);  // read a 256 MB buffer: L2 holds nothing of earlier kernels
 int tune_entries(qcd_ctx *c, int max, unsigned *keys, int *variant, int *bx, double *us);
 
 // force.cu

@@ -227,6 +227,31 @@ __device__ __forceinline__ df fma(df a, df b, df c)
     return fast_two_sum(s, f);
 }
 
+// Compensated dot products of double-float numbers (the Dot2 scheme of
+// Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26, 2005, with double-float inputs): each product's leading part
+// x.hi*y.hi is split exactly by TwoProduct (an fma), the leading parts are
+// summed with TwoSum, and every error term -- the products' rounding errors,
+// the cross terms x.hi*y.lo and x.lo*y.hi, the summation errors -- gathers in
+// one float that is folded in once, at the end.  About 12 FP32 instructions
+// per product instead of ~15 for a renormalised df fma, with the same ~2^-48
+// relative accuracy of the result.
+struct dacc {
+    float s = 0.f, e = 0.f;
+};
+__device__ __forceinline__ void dacc_fma(dacc &a, df x, df y)  // a += x*y
+{
+    const float p = x.hi * y.hi;
+    float c = fmaf(x.hi, y.hi, -p);
+    c = fmaf(x.hi, y.lo, c);
+    c = fmaf(x.lo, y.hi, c);
+    const float s = a.s + p;
+    const float bb = s - a.s;
+    a.e += ((a.s - (s - bb)) + (p - bb)) + c;
+    a.s = s;
+}
+__device__ __forceinline__ df dacc_get(const dacc &a) { return fast_two_sum(a.s, a.e); }
+
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
 __device__ __forceinline__ double to_d(df x) { return (double)x; }
@@ -349,12 +374,9 @@ struct Prec<QCD_F32> {
             p[soa(cb, 6, k)] = make_float4(a.r, a.i, b.r, b.i);
         }
     }
-    static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
+    // the 12 stored reals of a link (three float4: columns a, b) to the full U
+    static __device__ __forceinline__ void unpack_link(float4 f0, float4 f1, float4 f2, Link<T> &U)
     {
-        const float4 *p = (const float4 *)g.a[par];
-        float4 f0 = ld_stream(p + soa(cb, 12, mu * 3 + 0));
-        float4 f1 = ld_stream(p + soa(cb, 12, mu * 3 + 1));
-        float4 f2 = ld_stream(p + soa(cb, 12, mu * 3 + 2));
         U.u[0][0] = mk(f0.x, f0.y);
         U.u[1][0] = mk(f0.z, f0.w);
         U.u[2][0] = mk(f1.x, f1.y);
@@ -363,13 +385,20 @@ struct Prec<QCD_F32> {
         U.u[2][1] = mk(f2.z, f2.w);
         reconstruct(U);
     }
-    static __device__ __forceinline__ void load_clover(const CloverPtr &c, int par, int cb, int blk, T d[6], cx<T> o[15])
+    static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
     {
-        const float4 *p = (const float4 *)c.p[par];
+        const float4 *p = (const float4 *)g.a[par];
+        unpack_link(ld_stream(p + soa(cb, 12, mu * 3 + 0)), ld_stream(p + soa(cb, 12, mu * 3 + 1)),
+                    ld_stream(p + soa(cb, 12, mu * 3 + 2)), U);
+    }
+    // block blk of a site's clover entries, float4 k of the 18 fetched by src(k)
+    template <class Src>
+    static __device__ __forceinline__ void unpack_clover(const Src &src, int blk, T d[6], cx<T> o[15])
+    {
         float r[36];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            float4 f = ld_stream(p + soa(cb, 18, blk * 9 + k));
+            float4 f = src(blk * 9 + k);
             r[4 * k] = f.x;
             r[4 * k + 1] = f.y;
             r[4 * k + 2] = f.z;
@@ -379,6 +408,11 @@ struct Prec<QCD_F32> {
         for (int k = 0; k < 6; ++k) d[k] = r[k];
 #pragma unroll
         for (int k = 0; k < 15; ++k) o[k] = mk(r[6 + 2 * k], r[7 + 2 * k]);
+    }
+    static __device__ __forceinline__ void load_clover(const CloverPtr &c, int par, int cb, int blk, T d[6], cx<T> o[15])
+    {
+        const float4 *p = (const float4 *)c.p[par];
+        unpack_clover([&](int k) { return ld_stream(p + soa(cb, 18, k)); }, blk, d, o);
     }
 };
 
@@ -446,10 +480,9 @@ struct Prec<QCD_F16> {
         }
         v.norm[cb] = m;
     }
-    static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
+    // the 12 stored halves of a link (uint4 a0 a1 a2 b0, uint2 b1 b2) to the full U
+    static __device__ __forceinline__ void unpack_link(uint4 qa, uint2 qb, Link<T> &U)
     {
-        uint4 qa = ld_stream((const uint4 *)g.a[par] + soa(cb, 4, mu));
-        uint2 qb = ld_stream((const uint2 *)g.b[par] + soa(cb, 4, mu));
         U.u[0][0] = h2c(u2h(qa.x));
         U.u[1][0] = h2c(u2h(qa.y));
         U.u[2][0] = h2c(u2h(qa.z));
@@ -458,17 +491,28 @@ struct Prec<QCD_F16> {
         U.u[2][1] = h2c(u2h(qb.y));
         reconstruct(U);
     }
+    static __device__ __forceinline__ void load_link(const GaugePtr &g, int par, int cb, int mu, Link<T> &U)
+    {
+        unpack_link(ld_stream((const uint4 *)g.a[par] + soa(cb, 4, mu)), ld_stream((const uint2 *)g.b[par] + soa(cb, 4, mu)),
+                    U);
+    }
     static __device__ __forceinline__ void load_clover(const CloverPtr &c, int par, int cb, int blk, T d[6], cx<T> o[15])
+    {
+        const uint4 *p = (const uint4 *)c.p[par];
+        unpack_clover([&](int k) { return ld_stream(p + soa(cb, 9, k)); }, blk, d, o);
+    }
+    // block blk of a site's clover entries, uint4 k of the 9 fetched by src(k)
+    template <class Src>
+    static __device__ __forceinline__ void unpack_clover(const Src &src, int blk, T d[6], cx<T> o[15])
     {
         // 36 halves per block: 4.5 uint4; block 0 uses uint4 0..4 (first
         // half of 4), block 1 the second half of 4 and 5..8
-        const uint4 *p = (const uint4 *)c.p[par];
         float r[36];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             if (blk == 0 && k > 4) continue;
             if (blk == 1 && k < 4) continue;
-            uint4 q = ld_stream(p + soa(cb, 9, k));
+            uint4 q = src(k);
             unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -597,8 +641,8 @@ __device__ __forceinline__ void herm6(const T d[6], const cx<T> o[15], const cx<
 // components are chi_+ = (psi_up - psi_dn)/sqrt2 (gamma5 = +1) and
 // chi_- = (psi_up + psi_dn)/sqrt2; the 1/sqrt2 factors are combined into
 // the final 1/2.
-template <int P>
-__device__ __forceinline__ void apply_clover(const CloverPtr &c, int par, int cb, Spinor<typename Prec<P>::T> &s)
+template <int P, class CloverF>
+__device__ __forceinline__ void apply_clover_l(const CloverF &load, Spinor<typename Prec<P>::T> &s)
 {
     using T = typename Prec<P>::T;
     cx<T> xp[6], xm[6], yp[6], ym[6];
@@ -612,13 +656,13 @@ __device__ __forceinline__ void apply_clover(const CloverPtr &c, int par, int cb
     {
         T d[6];
         cx<T> o[15];
-        Prec<P>::load_clover(c, par, cb, 0, d, o);
+        load(0, d, o);
         herm6(d, o, xp, yp);
     }
     {
         T d[6];
         cx<T> o[15];
-        Prec<P>::load_clover(c, par, cb, 1, d, o);
+        load(1, d, o);
         herm6(d, o, xm, ym);
     }
     const T h = T(0.5);
@@ -629,6 +673,14 @@ __device__ __forceinline__ void apply_clover(const CloverPtr &c, int par, int cb
             s.s[a][i] = h * (yp[3 * a + i] + ym[3 * a + i]);
             s.s[a + 2][i] = h * (ym[3 * a + i] - yp[3 * a + i]);
         }
+}
+
+// the clover blocks read from global memory
+template <int P>
+__device__ __forceinline__ void apply_clover(const CloverPtr &c, int par, int cb, Spinor<typename Prec<P>::T> &s)
+{
+    using T = typename Prec<P>::T;
+    apply_clover_l<P>([&](int blk, T d[6], cx<T> o[15]) { Prec<P>::load_clover(c, par, cb, blk, d, o); }, s);
 }
 
 // ---------------------------------------------------------------- helpers

@@ -2,10 +2,11 @@
 // scalar updates that its last block performs.
 //
 // Each block reduces its threads' values (warp shuffles, then one warp over
-// the warp sums) and writes one partial per block; all blocks but the last
-// count themselves with a release add and retire, and the highest-indexed
-// block (dispatched last) waits, bounded, for that count, adds the partials
-// in block order and runs the finaliser on the solver state.  The sum order
+// the warp sums, the other warps leaving through a non-blocking barrier
+// arrival) and writes one partial per block; all blocks but the last count
+// themselves with a release add and retire, and the highest-indexed block
+// (dispatched last) waits, bounded, for that count, adds the partials in
+// block order and runs the finaliser on the solver state.  The sum order
 // depends only on the launch shape, so results repeat bit for bit from run
 // to run.  This replaces the paper's MPI_Allreduce of every dot product and
 // norm (Sec. IV-B).
@@ -153,6 +154,33 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < N; ++k) sh[wid][k] = (double)v[k];
+    if (blockIdx.x != gridDim.x - 1) {
+        // Every block but the last: warps 1.. post their sums and leave at
+        // once (bar.arrive does not wait; their output stores proceed), warp
+        // 0 waits for them (bar.sync on the same named barrier), adds the
+        // sums in warp order, writes the block's partial and counts it.
+        // Nothing holds a block at a full-block barrier.
+        if (wid != 0) {
+            asm volatile("bar.arrive 1, %0;" ::"r"(nthr) : "memory");
+            return;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+        double bsum[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            double t = lane < nw ? sh[lane][k] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+            bsum[k] = t;
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < N; ++k) ra.partials[(size_t)blockIdx.x * 4 + k] = bsum[k];
+            // the partial ordered before the count; no reply awaited
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ra.counter) : "memory");
+        }
+        return;
+    }
     __syncthreads();
     if (wid == 0) {
         double bsum[N];
@@ -166,26 +194,19 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < N; ++k) ra.partials[(size_t)blockIdx.x * 4 + k] = bsum[k];
-            if (blockIdx.x != gridDim.x - 1) {
-                // count this block, its partial ordered before the count; no
-                // waiting for a reply, so the block retires at once
-                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ra.counter) : "memory");
-            } else {
-                // the highest-indexed block is dispatched last: it waits
-                // (bounded) until every other block has counted
-                const unsigned want = gridDim.x - 1;
-                long long n = 0;
-                unsigned got;
-                for (;;) {
-                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(got) : "l"(ra.counter) : "memory");
-                    if (got >= want || ++n > (1ll << 26)) break;
-                    __nanosleep(32);
-                }
-                last = got >= want ? 1 : 0;
+            // the highest-indexed block is dispatched last: it waits
+            // (bounded) until every other block has counted
+            const unsigned want = gridDim.x - 1;
+            long long n = 0;
+            unsigned got;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(got) : "l"(ra.counter) : "memory");
+                if (got >= want || ++n > (1ll << 26)) break;
+                __nanosleep(32);
             }
+            last = got >= want ? 1 : 0;
         }
     }
-    if (blockIdx.x != gridDim.x - 1) return;
     __syncthreads();
     if (!last) {  // the other blocks never all counted: report, do not hang
         if (tid == 0) {

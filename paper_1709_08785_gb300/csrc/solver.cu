@@ -269,6 +269,27 @@ int true_residual(Solver &S, int P, HVec xe, HVec xo, HVec be, HVec bo)
     return QCD_OK;
 }
 
+// |b_e - (D x)_e|^2 = |b_e - F_ee x_e + kappa H_eo x_o|^2 in FP64, added to
+// aux->norm2[2], which the reconstruction pass (M_RECON) set to the odd rows'
+int residual_even(Solver &S, HVec xe, HVec xo)
+{
+    qcd_ctx *c = S.c;
+    StencilCall s;
+    s.prec = QCD_F64;
+    s.mode = M_FULL;
+    s.out_par = 0;
+    s.out = S.re;
+    s.in = xo;
+    s.y = xe;
+    s.a = -1.0;
+    s.cc = c->kappa;
+    s.z = S.be;
+    s.d = 1.0;
+    s.red = R_NORM;
+    s.red_args = RedArgs{c->partials, c->counters, S.aux, FIN_ADDN + 2};
+    return launch_stencil(c, s);
+}
+
 // x (canonical FP64, device) from the half vectors; when the caller's x is
 // in host memory, its copy is issued on the output stream at once, so that
 // it overlaps the true-residual check that follows.  A later emission (after
@@ -405,23 +426,31 @@ int solve_eo(Solver &S, const void *b, void *x, double tol)
         }
         S.info.outer_iters = h.iter;
         status = h.status;
-        // x_o = F_oo^-1 (b_o + kappa H_oe x_e)   (Eq. 7, Alg. 1 line 19)
+        // x_o = F_oo^-1 (b_o + kappa H_oe x_e)   (Eq. 7, Alg. 1 line 19); with
+        // an FP64 solution the same pass yields the odd rows of the FP64
+        // true residual b - D x, so that only the even rows need a pass of
+        // their own
         StencilCall s;
         s.prec = PX;
-        s.mode = M_SRC;
+        s.mode = PX == QCD_F64 ? M_RECON : M_SRC;
         s.out_par = 1;
         s.out = xoX;
         s.in = O.x;
         s.y = boX;
         s.a = 1.0;
         s.cc = c->kappa;
+        if (PX == QCD_F64) {
+            s.red = R_NORM;
+            s.red_args = RedArgs{c->partials, c->counters, S.aux, FIN_SETN + 2};  // |r_o|^2
+        }
         TRY(launch_stencil(c, s));
         if (PX != QCD_F64) {
             TRY(convert_half(c, O.x, xe64));
             TRY(convert_half(c, xoX, S.xo));
         }
         TRY(emit_x(c, xe64, S.xo, x));
-        TRY(true_residual(S, QCD_F64, xe64, S.xo, S.be, S.bo));
+        if (PX == QCD_F64) TRY(residual_even(S, xe64, S.xo));
+        else TRY(true_residual(S, QCD_F64, xe64, S.xo, S.be, S.bo));
         TRY(read_state(c, ST_AUX, &ha));
         S.info.true_resid = resid_ratio(ha);
         if (!std::isfinite(S.info.true_resid)) {

@@ -5,6 +5,7 @@
 //                                             with the dot products of Alg. 2 fused)
 //   M_SRC   out = F^-1 (a*y + cc*H in)       (b^_e, Eq. 6, and x_o, Eq. 7)
 //   M_FULL  out = a*F y + cc*H in + d*z      (D = F - kappa H on one parity, residuals)
+//   M_RECON out = F^-1 (a*y + cc*H in) and |a*y + cc*H in - F out|^2 (FP64 only)
 //
 // One thread computes one output site (and one right-hand side: the
 // right-hand sides of a site sit in the same block so that its links and
@@ -47,7 +48,8 @@ double stencil_bytes(const qcd_ctx *c, const StencilCall &sc)
     const int nrhs = sc.nrhs < 1 ? 1 : sc.nrhs;
     double per_site = nrhs * 2 * sp + 8 * lk;  // in, out, links
     if (sc.mode != M_HOP) per_site += cl;
-    if (sc.mode == M_DHAT || sc.mode == M_SRC || sc.mode == M_FULL) per_site += nrhs * sp;  // y
+    if (sc.mode == M_DHAT || sc.mode == M_SRC || sc.mode == M_FULL || sc.mode == M_RECON) per_site += nrhs * sp;  // y
+    if (sc.mode == M_RECON) per_site += cl;  // F as well as F^-1
     if (sc.d != 0.0 && (sc.mode == M_DHAT || sc.mode == M_FULL)) per_site += nrhs * sp;   // z
     if (sc.red == R_DOT_AUX || (sc.red == R_OMEGA && sc.aux.p != sc.y.p)) per_site += nrhs * sp;
     return per_site * c->g.Vh;
@@ -67,6 +69,7 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
         A.U.a[par] = p == QCD_F64 ? c->U64[par] : p == QCD_F32 ? c->U32[par] : p == QCD_DF64 ? c->UDF[par] : c->U16a[par];
         A.U.b[par] = c->U16b[par];
         A.C.p[par] = (sc.mode == M_FULL) ? c->C[p][par] : c->Ci[p][par];
+        A.Cf.p[par] = c->C[p][par];
     }
     A.out = sc.out.sp();
     A.in = sc.in.sp();

@@ -12,7 +12,8 @@ namespace qcd {
 // S = +1: projector (1 - gamma_mu);  S = -1: (1 + gamma_mu).
 // For mu = x, y, z: (1 - S g_k) psi = (h, -S i s_k h) with
 // h = psi_up + S i s_k psi_dn.  For mu = t: (1 - S g_t) keeps the lower
-// (S = +1) or upper (S = -1) pair, times 2.
+// (S = +1) or upper (S = -1) pair, times 2; the factor 2 is applied in the
+// expansion (exact, so the result is the same to the bit).
 template <int MU, int S, class T>
 __device__ __forceinline__ void project(const Spinor<T> &p, cx<T> h[2][3])
 {
@@ -28,11 +29,18 @@ __device__ __forceinline__ void project(const Spinor<T> &p, cx<T> h[2][3])
             h[0][i] = S > 0 ? p.s[0][i] + ti(p.s[2][i]) : p.s[0][i] - ti(p.s[2][i]);
             h[1][i] = S > 0 ? p.s[1][i] - ti(p.s[3][i]) : p.s[1][i] + ti(p.s[3][i]);
         } else {
-            const T two = T(2);
-            h[0][i] = S > 0 ? two * p.s[2][i] : two * p.s[0][i];
-            h[1][i] = S > 0 ? two * p.s[3][i] : two * p.s[1][i];
+            h[0][i] = S > 0 ? p.s[2][i] : p.s[0][i];
+            h[1][i] = S > 0 ? p.s[3][i] : p.s[1][i];
         }
     }
+}
+
+// 2 a, exactly
+template <class T>
+__device__ __forceinline__ cx<T> twice(cx<T> a)
+{
+    if constexpr (std::is_same<T, df>::value) return mk(df(2.f * a.r.hi, 2.f * a.r.lo), df(2.f * a.i.hi, 2.f * a.i.lo));
+    else return mk(T(2) * a.r, T(2) * a.i);
 }
 
 // acc += expansion of the projected, colour-multiplied pair g
@@ -41,13 +49,13 @@ __device__ __forceinline__ void expand(Spinor<T> &acc, const cx<T> g[2][3])
 {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        if (MU == 3) {
+        if (MU == 3) {  // the projector's factor 2 (see project)
             if (S > 0) {
-                acc.s[2][i] = acc.s[2][i] + g[0][i];
-                acc.s[3][i] = acc.s[3][i] + g[1][i];
+                acc.s[2][i] = acc.s[2][i] + twice(g[0][i]);
+                acc.s[3][i] = acc.s[3][i] + twice(g[1][i]);
             } else {
-                acc.s[0][i] = acc.s[0][i] + g[0][i];
-                acc.s[1][i] = acc.s[1][i] + g[1][i];
+                acc.s[0][i] = acc.s[0][i] + twice(g[0][i]);
+                acc.s[1][i] = acc.s[1][i] + twice(g[1][i]);
             }
         } else {
             acc.s[0][i] = acc.s[0][i] + g[0][i];
@@ -77,15 +85,16 @@ __device__ __forceinline__ void expand_w(Spinor<T> &acc, const cx<T> g[2][3], T 
     auto add = [](cx<T> &a, const cx<T> &b, T f) { a = mk(::fmaf(f, b.r, a.r), ::fmaf(f, b.i, a.i)); };
     // a += f * (i b) = (a.r - f b.i, a.i + f b.r)
     auto addi = [](cx<T> &a, const cx<T> &b, T f) { a = mk(::fmaf(-f, b.i, a.r), ::fmaf(f, b.r, a.i)); };
+    const T w2 = T(2) * w;  // mu = t: the projector's factor 2 (see project)
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         if (MU == 3) {
             if (S > 0) {
-                add(acc.s[2][i], g[0][i], w);
-                add(acc.s[3][i], g[1][i], w);
+                add(acc.s[2][i], g[0][i], w2);
+                add(acc.s[3][i], g[1][i], w2);
             } else {
-                add(acc.s[0][i], g[0][i], w);
-                add(acc.s[1][i], g[1][i], w);
+                add(acc.s[0][i], g[0][i], w2);
+                add(acc.s[1][i], g[1][i], w2);
             }
         } else {
             add(acc.s[0][i], g[0][i], w);
@@ -104,10 +113,42 @@ __device__ __forceinline__ void expand_w(Spinor<T> &acc, const cx<T> g[2][3], T 
     }
 }
 
+// complex double-float products gathered in compensated accumulators
+// (dacc): a += x*y, a += conj(x)*y
+__device__ __forceinline__ void cdacc_fma(dacc &ar, dacc &ai, const cx<df> &x, const cx<df> &y)
+{
+    dacc_fma(ar, x.r, y.r);
+    dacc_fma(ar, -x.i, y.i);
+    dacc_fma(ai, x.r, y.i);
+    dacc_fma(ai, x.i, y.r);
+}
+__device__ __forceinline__ void cdacc_fmac(dacc &ar, dacc &ai, const cx<df> &x, const cx<df> &y)
+{
+    dacc_fma(ar, x.r, y.r);
+    dacc_fma(ar, x.i, y.i);
+    dacc_fma(ai, x.r, y.i);
+    dacc_fma(ai, -x.i, y.r);
+}
+
 // g = U h  or  g = U^dag h, for both spin rows
 template <bool DAG, class T>
 __device__ __forceinline__ void colour_mul(const Link<T> &U, const cx<T> h[2][3], cx<T> g[2][3])
 {
+    if constexpr (std::is_same<T, df>::value) {  // each row a compensated dot product
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                dacc sr, si;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (DAG) cdacc_fmac(sr, si, U.u[j][i], h[a][j]);
+                    else cdacc_fma(sr, si, U.u[i][j], h[a][j]);
+                }
+                g[a][i] = mk(dacc_get(sr), dacc_get(si));
+            }
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
@@ -122,12 +163,25 @@ __device__ __forceinline__ void colour_mul(const Link<T> &U, const cx<T> h[2][3]
         }
 }
 
-template <int P, int MU, int SF>
-__device__ __forceinline__ void hop_dir(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par, int cb,
+// The links of a site's eight hops, read from global memory: the forward
+// link U_mu(n) at the site itself, the backward one U_mu(n - mu) at the
+// neighbour (the other parity)
+template <int P>
+struct GlobalLinks {
+    const GaugePtr &U;  // the kernel's parameter, not a copy in registers
+    int out_par, cb;
+    template <int MU, int BWD>
+    __device__ __forceinline__ void load(int nb, Link<typename Prec<P>::T> &L) const
+    {
+        Prec<P>::load_link(U, BWD ? 1 - out_par : out_par, BWD ? nb : cb, MU, L);
+    }
+};
+
+template <int P, int MU, int SF, class LinkF>
+__device__ __forceinline__ void hop_dir(const Geom &g, const LinkF &links, const SpinorPtr &in, int out_par, int cb,
                                         int lex, const int c[4], Spinor<typename Prec<P>::T> &acc)
 {
     using T = typename Prec<P>::T;
-    const int in_par = 1 - out_par;
     {  // forward hop: (1 - SF g_mu) U_mu(n) psi(n + mu)
         const int nb = lex_hop(g, lex, c, MU, +1) >> 1;
         const bool flip = MU == 3 && g.t_bc < 0 && c[3] == g.L[3] - 1;
@@ -137,13 +191,13 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugePtr &U, const 
         if constexpr (P == QCD_F16) {  // the neighbour's norm and the boundary sign go into the accumulation
             const T w = Prec<P>::load_raw(in, nb, psi);
             project<MU, SF>(psi, h);
-            Prec<P>::load_link(U, out_par, cb, MU, L);
+            links.template load<MU, 0>(nb, L);
             colour_mul<false>(L, h, q);
             expand_w<MU, SF>(acc, q, flip ? -w : w);
         } else {
             Prec<P>::load(in, nb, psi);
             project<MU, SF>(psi, h);
-            Prec<P>::load_link(U, out_par, cb, MU, L);
+            links.template load<MU, 0>(nb, L);
             colour_mul<false>(L, h, q);
             if (flip) {
 #pragma unroll
@@ -163,13 +217,13 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugePtr &U, const 
         if constexpr (P == QCD_F16) {
             const T w = Prec<P>::load_raw(in, nb, psi);
             project<MU, -SF>(psi, h);
-            Prec<P>::load_link(U, in_par, nb, MU, L);
+            links.template load<MU, 1>(nb, L);
             colour_mul<true>(L, h, q);
             expand_w<MU, -SF>(acc, q, flip ? -w : w);
         } else {
             Prec<P>::load(in, nb, psi);
             project<MU, -SF>(psi, h);
-            Prec<P>::load_link(U, in_par, nb, MU, L);
+            links.template load<MU, 1>(nb, L);
             colour_mul<true>(L, h, q);
             if (flip) {
 #pragma unroll
@@ -184,9 +238,9 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const GaugePtr &U, const 
 
 // acc = H in at site cb of parity out_par (DAG: gamma5 H gamma5, i.e. the
 // projector signs exchanged)
-template <int P, bool DAG>
-__device__ __forceinline__ void hopping(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par, int cb,
-                                        Spinor<typename Prec<P>::T> &acc)
+template <int P, bool DAG, class LinkF>
+__device__ __forceinline__ void hopping_l(const Geom &g, const LinkF &links, const SpinorPtr &in, int out_par, int cb,
+                                          Spinor<typename Prec<P>::T> &acc)
 {
     using T = typename Prec<P>::T;
     int c[4];
@@ -197,10 +251,131 @@ __device__ __forceinline__ void hopping(const Geom &g, const GaugePtr &U, const 
 #pragma unroll
         for (int i = 0; i < 3; ++i) acc.s[a][i] = mk(T(0), T(0));
     constexpr int SF = DAG ? -1 : 1;
-    hop_dir<P, 0, SF>(g, U, in, out_par, cb, lex, c, acc);
-    hop_dir<P, 1, SF>(g, U, in, out_par, cb, lex, c, acc);
-    hop_dir<P, 2, SF>(g, U, in, out_par, cb, lex, c, acc);
-    hop_dir<P, 3, SF>(g, U, in, out_par, cb, lex, c, acc);
+    hop_dir<P, 0, SF>(g, links, in, out_par, cb, lex, c, acc);
+    hop_dir<P, 1, SF>(g, links, in, out_par, cb, lex, c, acc);
+    hop_dir<P, 2, SF>(g, links, in, out_par, cb, lex, c, acc);
+    hop_dir<P, 3, SF>(g, links, in, out_par, cb, lex, c, acc);
+}
+
+template <int P, bool DAG>
+__device__ __forceinline__ void hopping(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par, int cb,
+                                        Spinor<typename Prec<P>::T> &acc)
+{
+    hopping_l<P, DAG>(g, GlobalLinks<P>{U, out_par, cb}, in, out_par, cb, acc);
+}
+
+// ---- software-pipelined hops (FP32 / FP16) -----------------------------------
+// The eight hops of a site in a fixed order d = 2 mu + bwd, with the raw
+// loads (neighbour spinor, link) of hop d + 1 issued before hop d computes:
+// two hops' loads in flight per thread instead of one, which halves the
+// chain of memory latencies a site waits through (the autotuner's
+// "pipelined" variant, at the cost of the registers holding the raw data).
+template <int P>
+struct RawHop;
+template <>
+struct RawHop<QCD_F32> {
+    float4 s[6], l[3];
+};
+template <>
+struct RawHop<QCD_F16> {
+    uint4 s[3];
+    float n;
+    uint4 la;
+    uint2 lb;
+};
+
+template <int P, int D>
+__device__ __forceinline__ void raw_hop_load(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par,
+                                             int cb, int lex, const int c[4], RawHop<P> &R)
+{
+    constexpr int MU = D >> 1, BWD = D & 1;
+    const int nb = lex_hop(g, lex, c, MU, BWD ? -1 : +1) >> 1;
+    const int lpar = BWD ? 1 - out_par : out_par, lsite = BWD ? nb : cb;
+    if constexpr (P == QCD_F32) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) R.s[k] = __ldg((const float4 *)in.p + soa(nb, 6, k));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) R.l[k] = ld_stream((const float4 *)U.a[lpar] + soa(lsite, 12, MU * 3 + k));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) R.s[k] = __ldg((const uint4 *)in.p + soa(nb, 3, k));
+        R.n = __ldg(in.norm + nb);
+        R.la = ld_stream((const uint4 *)U.a[lpar] + soa(lsite, 4, MU));
+        R.lb = ld_stream((const uint2 *)U.b[lpar] + soa(lsite, 4, MU));
+    }
+}
+
+template <int P, int D, int SF>
+__device__ __forceinline__ void raw_hop_apply(const Geom &g, const int c[4], const RawHop<P> &R, Spinor<float> &acc)
+{
+    constexpr int MU = D >> 1, BWD = D & 1;
+    constexpr int S = BWD ? -SF : SF;  // forward (1 - SF g_mu), backward (1 + SF g_mu)
+    const bool flip = MU == 3 && g.t_bc < 0 && (BWD ? c[3] == 0 : c[3] == g.L[3] - 1);
+    Spinor<float> psi;
+    Link<float> L;
+    cx<float> h[2][3], q[2][3];
+    if constexpr (P == QCD_F32) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            psi.s[(2 * k) / 3][(2 * k) % 3] = mk(R.s[k].x, R.s[k].y);
+            psi.s[(2 * k + 1) / 3][(2 * k + 1) % 3] = mk(R.s[k].z, R.s[k].w);
+        }
+        Prec<P>::unpack_link(R.l[0], R.l[1], R.l[2], L);
+        project<MU, S>(psi, h);
+        colour_mul<BWD == 1>(L, h, q);
+        if (flip) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) q[a][i] = -q[a][i];
+        }
+        expand<MU, S>(acc, q);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const unsigned w[4] = {R.s[k].x, R.s[k].y, R.s[k].z, R.s[k].w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cc = 4 * k + j;
+                psi.s[cc / 3][cc % 3] = h2c(u2h(w[j]));
+            }
+        }
+        Prec<P>::unpack_link(R.la, R.lb, L);
+        project<MU, S>(psi, h);
+        colour_mul<BWD == 1>(L, h, q);
+        expand_w<MU, S>(acc, q, flip ? -R.n : R.n);  // the neighbour's norm and the boundary sign
+    }
+}
+
+template <int P, bool DAG>
+__device__ __forceinline__ void hopping_pipe(const Geom &g, const GaugePtr &U, const SpinorPtr &in, int out_par,
+                                             int cb, Spinor<float> &acc)
+{
+    int c[4];
+    site_coords(g, out_par, cb, c);
+    const int lex = lex_of(g, c);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc.s[a][i] = mk(0.f, 0.f);
+    constexpr int SF = DAG ? -1 : 1;
+    RawHop<P> R0, R1;
+    raw_hop_load<P, 0>(g, U, in, out_par, cb, lex, c, R0);
+    raw_hop_load<P, 1>(g, U, in, out_par, cb, lex, c, R1);
+    raw_hop_apply<P, 0, SF>(g, c, R0, acc);
+    raw_hop_load<P, 2>(g, U, in, out_par, cb, lex, c, R0);
+    raw_hop_apply<P, 1, SF>(g, c, R1, acc);
+    raw_hop_load<P, 3>(g, U, in, out_par, cb, lex, c, R1);
+    raw_hop_apply<P, 2, SF>(g, c, R0, acc);
+    raw_hop_load<P, 4>(g, U, in, out_par, cb, lex, c, R0);
+    raw_hop_apply<P, 3, SF>(g, c, R1, acc);
+    raw_hop_load<P, 5>(g, U, in, out_par, cb, lex, c, R1);
+    raw_hop_apply<P, 4, SF>(g, c, R0, acc);
+    raw_hop_load<P, 6>(g, U, in, out_par, cb, lex, c, R0);
+    raw_hop_apply<P, 5, SF>(g, c, R1, acc);
+    raw_hop_load<P, 7>(g, U, in, out_par, cb, lex, c, R1);
+    raw_hop_apply<P, 6, SF>(g, c, R0, acc);
+    raw_hop_apply<P, 7, SF>(g, c, R1, acc);
 }
 
 // ---- rolled forms ----------------------------------------------------------
@@ -287,6 +462,21 @@ __device__ void hopping_rolled(const Geom &g, const GaugePtr &U, const SpinorPtr
 template <class T>
 __device__ void herm6_rolled(const T d[6], const cx<T> o[15], const cx<T> x[6], cx<T> y[6])
 {
+    if constexpr (std::is_same<T, df>::value) {  // each row a compensated dot product
+#pragma unroll 1
+        for (int i = 0; i < 6; ++i) {
+            dacc sr, si;
+            dacc_fma(sr, d[i], x[i].r);
+            dacc_fma(si, d[i], x[i].i);
+#pragma unroll 1
+            for (int j = 0; j < 6; ++j) {
+                if (j < i) cdacc_fma(sr, si, o[i * (i - 1) / 2 + j], x[j]);
+                else if (j > i) cdacc_fmac(sr, si, o[j * (j - 1) / 2 + i], x[j]);
+            }
+            y[i] = mk(dacc_get(sr), dacc_get(si));
+        }
+        return;
+    }
 #pragma unroll 1
     for (int i = 0; i < 6; ++i) {
         cx<T> a = mk(d[i] * x[i].r, d[i] * x[i].i);
@@ -348,6 +538,7 @@ struct StencilArgs {
     Geom g;
     GaugePtr U;
     CloverPtr C;
+    CloverPtr Cf;  // the clover term F itself, for M_RECON (C holds F^-1 there)
     SpinorPtr out, in, y, aux, z;
     int out_par;
     double a, cc, d;

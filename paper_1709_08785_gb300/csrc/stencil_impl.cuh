@@ -6,6 +6,8 @@
 //                                             with the dot products of Alg. 2 fused)
 //   M_SRC   out = F^-1 (a*y + cc*H in)       (b^_e, Eq. 6, and x_o, Eq. 7)
 //   M_FULL  out = a*F y + cc*H in + d*z      (D = F - kappa H on one parity, residuals)
+//   M_RECON out = F^-1 u, u = a*y + cc*H in, with |u - F out|^2 reduced (x_o of
+//                                             Eq. 7 and the odd part of b - D x in one pass)
 //
 // One thread computes one output site (and one right-hand side: the
 // right-hand sides of a site sit in the same block so that its links and
@@ -40,19 +42,23 @@ __device__ __forceinline__ void omega_sums(const Spinor<T> &o_, const Spinor<T> 
 }
 
 // One output site cb (right-hand side r): the hops, the mode's epilogue, the
-// site's contributions to the fused reductions.
-template <int P, int MODE, int RED, bool DAG, class RA>
-__device__ __forceinline__ void stencil_site(const StencilArgs &A, int cb, int r, RA red[4])
+// site's contributions to the fused reductions.  The result is left in acc
+// for the caller to store (true), so that a kernel with a grid reduction
+// can publish its block's partial before its output stores are issued.
+// hop(acc) computes acc = H in at the site, clov(x) applies the site's clover
+// term (F^-1, or F for M_FULL) to x in place: from global memory, or from
+// the staged shared-memory copies.
+template <int P, int MODE, int RED, bool DAG, class RA, class HopF, class CloF>
+__device__ __forceinline__ bool stencil_site(const StencilArgs &A, int cb, int r, RA red[4],
+                                             Spinor<typename Prec<P>::T> &acc, const HopF &hop, const CloF &clov)
 {
     using T = typename Prec<P>::T;
-    const SpinorPtr in = rhs_ptr(A.in, r, A.rhs_stride, A.norm_stride);
     const SpinorPtr out = rhs_ptr(A.out, r, A.rhs_stride, A.norm_stride);
-    Spinor<T> acc;
-    hopping_any<P, DAG>(A.g, A.U, in, A.out_par, cb, acc);
+    hop(acc);
     if (MODE == M_MULT) {
-        clover_any<P>(A.C,A.out_par, cb, acc);
+        clov(acc);
     } else if (MODE == M_DHAT) {
-        clover_any<P>(A.C,A.out_par, cb, acc);
+        clov(acc);
         Spinor<T> y;
         Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
         axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
@@ -69,14 +75,37 @@ __device__ __forceinline__ void stencil_site(const StencilArgs &A, int cb, int r
         Spinor<T> y;
         Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
         axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);
-        clover_any<P>(A.C,A.out_par, cb, acc);
+        clov(acc);
+    } else if (MODE == M_RECON) {
+        // x_o = F^-1 u with u = b_o + kappa H_oe x_e, and the odd rows of the
+        // residual, b_o - (F_oo x_o - kappa H_oe x_e) = u - F x_o, from the
+        // same hopping term
+        Spinor<T> y;
+        Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
+        axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), y);  // u
+        Spinor<T> xo = acc;
+        clover_any<P>(A.C, A.out_par, cb, xo);
+        Prec<P>::store(out, cb, xo);
+        clover_any<P>(A.Cf, A.out_par, cb, xo);  // F x_o
+        if (RED == R_NORM) {
+            T nn = 0;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const cx<T> d = acc.s[s][i] - xo.s[s][i];
+                    nn += d.r * d.r + d.i * d.i;
+                }
+            red[0] += acc_cast<RA>(nn);
+        }
+        return false;
     } else if (MODE == M_FULL) {
         // also the second half of the gamma5-hermitian S_ee = F_ee - k^2 H_eo F_oo^-1 H_oe
         // (a = 1, cc = -k^2, y = the operator's input), with its dot products
         Spinor<T> y;
         Prec<P>::load(rhs_ptr(A.y, r, A.rhs_stride, A.norm_stride), cb, y);
         Spinor<T> fy = y;
-        clover_any<P>(A.C,A.out_par, cb, fy);
+        clov(fy);
         axpby_sp(acc, sarg<T>(A.cc, A.ccf), acc, sarg<T>(A.a, A.af), fy);
         if (A.has_z) {
             Spinor<T> z;
@@ -110,7 +139,7 @@ __device__ __forceinline__ void stencil_site(const StencilArgs &A, int cb, int r
             for (int i = 0; i < 3; ++i) nn += acc.s[s][i].r * acc.s[s][i].r + acc.s[s][i].i * acc.s[s][i].i;
         red[0] += acc_cast<RA>(nn);
     }
-    Prec<P>::store(out, cb, acc);
+    return true;
 }
 
 template <int P, int MODE, int RED, bool DAG>
@@ -128,8 +157,20 @@ __device__ __forceinline__ void stencil_body(const StencilArgs &A)
     using RA = typename std::conditional<P == QCD_F32 || P == QCD_F16, float, double>::type;
     RA red[4] = {RA(0), RA(0), RA(0), RA(0)};
     const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cb < A.g.Vh) stencil_site<P, MODE, RED, DAG>(A, cb, r, red);
+    using T = typename Prec<P>::T;
+    Spinor<T> acc;
+    bool pending = false;
+    if (cb < A.g.Vh) {
+        const SpinorPtr in = rhs_ptr(A.in, r, A.rhs_stride, A.norm_stride);
+        pending = stencil_site<P, MODE, RED, DAG>(
+            A, cb, r, red, acc, [&](Spinor<T> &a) { hopping_any<P, DAG>(A.g, A.U, in, A.out_par, cb, a); },
+            [&](Spinor<T> &x) { clover_any<P>(A.C, A.out_par, cb, x); });
+    }
     if constexpr (RED != R_NONE) grid_reduce<RED == R_OMEGA ? 3 : RED == R_DOT_AUX ? 2 : 1>(red, A.red);
+    // the output after the partial: the release that publishes the block's
+    // partial does not wait for these stores (the next kernel, not the
+    // finishing block, reads them)
+    if (pending) Prec<P>::store(rhs_ptr(A.out, r, A.rhs_stride, A.norm_stride), cb, acc);
 }
 
 // Two register budgets of the same kernel; the autotuner picks one per
@@ -148,6 +189,37 @@ __global__ void __maxnreg__(80) stencil_kernel_r80(StencilArgs A)
     stencil_body<P, MODE, RED, DAG>(A);
 }
 
+// The pipelined variant (FP32 / FP16, one right-hand side): the hops of
+// hopping_pipe, the clover term from global memory; the compiler's register
+// budget (the prefetched raw data of one hop lives beside the current one)
+template <int P, int MODE, int RED, bool DAG>
+__device__ __forceinline__ void stencil_body_pipe(const StencilArgs &A)
+{
+    pdl_enter();
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    if (A.done && *A.done) {
+        if (A.skip && lead) *A.skip = 1;
+        return;
+    }
+    if (A.skip && lead) *A.skip = 0;
+    float red[4] = {0.f, 0.f, 0.f, 0.f};
+    const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+    Spinor<float> acc;
+    bool pending = false;
+    if (cb < A.g.Vh)
+        pending = stencil_site<P, MODE, RED, DAG>(
+            A, cb, 0, red, acc, [&](Spinor<float> &a) { hopping_pipe<P, DAG>(A.g, A.U, A.in, A.out_par, cb, a); },
+            [&](Spinor<float> &x) { clover_any<P>(A.C, A.out_par, cb, x); });
+    if constexpr (RED != R_NONE) grid_reduce<RED == R_OMEGA ? 3 : RED == R_DOT_AUX ? 2 : 1>(red, A.red);
+    if (pending) Prec<P>::store(A.out, cb, acc);
+}
+
+template <int P, int MODE, int RED, bool DAG>
+__global__ void __launch_bounds__(256) stencil_kernel_pipe(StencilArgs A)
+{
+    if constexpr (P == QCD_F32 || P == QCD_F16) stencil_body_pipe<P, MODE, RED, DAG>(A);
+}
+
 // DF64 (arithmetic-bound, ~165 registers by default): a 128-register cap
 // gives four 128-thread blocks per SM instead of three
 template <int P, int MODE, int RED, bool DAG>
@@ -164,6 +236,12 @@ static void launch_t(const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s
         if (variant == 1) {
             launch_pdl(stencil_kernel_r80<P, MODE, RED, DAG>, grid, block, 0, s, A);
             return;
+        }
+        if constexpr (MODE == M_MULT || MODE == M_DHAT || MODE == M_FULL) {
+            if (variant == 2 && block.y == 1 && block.x <= 256) {
+                launch_pdl(stencil_kernel_pipe<P, MODE, RED, DAG>, grid, block, 0, s, A);
+                return;
+            }
         }
     }
     if constexpr (P == QCD_DF64) {
@@ -206,6 +284,9 @@ int dispatch(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block,
     QCD_CASE(M_FULL, R_NORM)
     QCD_CASE(M_FULL, R_DOT_AUX)
     QCD_CASE(M_FULL, R_OMEGA)
+    if constexpr (P == QCD_F64) {  // the FP64 reconstruction with its residual
+        QCD_CASE(M_RECON, R_NORM)
+    }
 #undef QCD_CASE
     set_error_message("unsupported stencil mode %d / reduction %d", sc.mode, sc.red);
     return QCD_EINVAL;

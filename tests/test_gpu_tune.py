@@ -29,8 +29,11 @@ def test_autotune_cache_and_parity(tmp_path):
     def mrhs(e):  # the shared-memory multi-RHS kernel: FP32 hopping / MULT, several RHS
         return e["prec"] == 1 and e["nrhs"] > 1 and e["red"] == 0 and e["mode"] in (0, 1)
 
+    def piped(e):  # FP32 / FP16 single-RHS MULT and D^ halves: also the pipelined-hop kernel
+        return e["prec"] in (1, 2) and e["nrhs"] == 1 and e["mode"] in (1, 2, 4)
+
     for e in entries:
-        assert e["variant"] in (0, 1)
+        assert e["variant"] in ((0, 1, 2) if piped(e) else (0, 1))
         if mrhs(e):  # threads = right-hand sides per block, a divisor of nrhs
             assert e["nrhs"] % e["threads"] == 0
         else:
@@ -68,12 +71,15 @@ def test_autotune_cache_and_parity(tmp_path):
     ctx2.close()
 
 
-def test_forced_launch_shapes_keep_parity(tmp_path):
+@pytest.mark.parametrize("cap", [1, 2])
+def test_forced_launch_shapes_keep_parity(tmp_path, cap):
     """Every tuned entry rewritten to 64 (32 with several right-hand sides)
-    sites per block and, where it exists, the capped register budget, and
-    the multi-RHS kernel to a tile of 4 right-hand sides; a context that
-    reads that cache runs those shapes, and the operators and a solve still
-    match the oracle."""
+    sites per block and, where it exists, the capped register budget (cap 1)
+    or, for the FP32 / FP16 MULT and D^ halves, the pipelined-hop kernel
+    (cap 2; the 80 / 128 cap elsewhere), and the multi-RHS kernel to a tile
+    of 4 right-hand sides;
+    a context that reads that cache runs those shapes, and the operators and
+    a solve still match the oracle."""
     from paper_1709_08785_gb300 import qcd
 
     dims, kappa, csw, t_bc = (6, 2, 4, 10), 0.124, 1.6, -1  # Vh = 240: ragged blocks
@@ -87,8 +93,10 @@ def test_forced_launch_shapes_keep_parity(tmp_path):
     for k, (variant, bx, us) in list(data.items()):
         key = int(k.rsplit("|", 1)[1])
         prec, mode, red, nrhs = key & 3, (key >> 2) & 7, (key >> 5) & 3, key >> 8
-        if prec == 1 and nrhs > 1 and red == 0 and mode in (0, 1):
-            data[k] = [variant, 4, us]
+        if prec == 1 and nrhs > 1 and red == 0 and mode in (0, 1):  # multi-RHS kernel, its three variants
+            data[k] = [{1: 1, 2: 0}[cap], 4, us]
+        elif prec in (1, 2) and nrhs == 1 and mode in (1, 2, 4):
+            data[k] = [cap, 64, us]
         else:
             data[k] = [0 if prec == 0 else 1, 64 if nrhs == 1 else 32, us]
     # the cache's own layout: one entry per line
@@ -113,6 +121,14 @@ def test_forced_launch_shapes_keep_parity(tmp_path):
         torch.cuda.synchronize()
         got = out.cpu().numpy().astype(np.complex128)
         assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol, prec
+    want = oracle.schur_ee(dims, t_bc, U, F, Fi, kappa, v)
+    for prec, tol, dt in ((1, 2e-6, torch.complex64), (2, 2e-3, torch.complex64)):
+        inp = torch.from_numpy(v).to(dt).cuda()
+        out = torch.zeros_like(inp)
+        ctx.schur_ee(out, inp, prec)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol, prec
     # 12 right-hand sides through the tiled kernel, against single-RHS oracle MULTs
     vs = np.stack([inputs.gaussian_source(dims, 96 + k)[:Vh] for k in range(12)])
     inp = torch.from_numpy(vs).to(torch.complex64).cuda()
@@ -126,7 +142,8 @@ def test_forced_launch_shapes_keep_parity(tmp_path):
     b = inputs.gaussian_source(dims, 97)
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bd)
-    info = ctx.solve(bd, x, tol=1e-12, precision_levels=2)
-    assert info["status"] == 0
-    assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
+    for levels, herm in ((2, 0), (3, 0), (2, 1)):
+        info = ctx.solve(bd, x, tol=1e-12, precision_levels=levels, eo_hermitian=herm)
+        assert info["status"] == 0
+        assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
     ctx.close()
