@@ -275,9 +275,15 @@ int qcd_solve_adjoint(qcd_ctx *ctx, const void *g, void *lam, double tol, const 
  * device complex128 [V][4][3]; G: device complex128 [V][4][3][3]. FP64. */
 int qcd_force(qcd_ctx *ctx, const void *U, const void *x, const void *lam, void *G);
 
-/* Kernel timing: when enabled, each launch of the fused MULT kernel
- * (and of the other solver kernels) is bracketed by CUDA events on the
- * context stream; qcd_kernel_stats sums them. */
+/* Kernel timing.  qcd_set_profiling(ctx, 1): each launch of the operator
+ * and BLAS kernels is bracketed by CUDA events on the context stream and
+ * qcd_kernel_stats sums them by class (a bracketed launch cannot overlap
+ * its predecessor, so its time includes its own launch latency).
+ * qcd_set_profiling(ctx, 2): chunk timing -- one event pair around each
+ * chunk of FP32-level BiCGStab iterations the solver queues, the launches
+ * inside left back to back as in any solve; the class QCD_K_INNER_ITER then
+ * sums whole iterations (launches = iterations, their algorithmic bytes).
+ * 0 turns timing off.  QCD_EINVAL for other values. */
 typedef enum {
     QCD_K_MULT_F64 = 0,  /* stencil kernels (MULT, D^, b^, x_o, D), by precision; */
     QCD_K_MULT_F32 = 1,  /* FP32: all but the second half of D^, which is QCD_K_DHAT_F32 */
@@ -287,7 +293,9 @@ typedef enum {
     QCD_K_DHAT_F32 = 5,  /* FP32 second half of D^ with its fused update and dot products */
     QCD_K_MULT_DF64 = 6, /* DF64 stencil kernels */
     QCD_K_BLAS_F32 = 7,  /* fused BLAS-1 + reduction kernels of the FP32 level */
-    QCD_K_COUNT = 8
+    QCD_K_INNER_ITER = 8, /* whole FP32-level BiCGStab iterations (chunk timing, see
+                             qcd_set_profiling): launches = iterations */
+    QCD_K_COUNT = 9
 } qcd_kernel_class;
 
 typedef struct {

@@ -97,6 +97,7 @@ int ensure_staging(qcd_ctx *c, size_t bytes)
 ProfScope::ProfScope(qcd_ctx *c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_)
 {
     c->launches += 1;
+    if (c->chunk_timing) c->chunk_bytes += bytes;
     if (!c->profiling) return;
     if ((int)c->pending.size() >= PROF_CAP) collect_profile(c);
     const size_t need = 2;
@@ -248,6 +249,8 @@ extern "C" int qcd_destroy(qcd_ctx *c)
         cudaStreamDestroy(c->out_stream);
     }
     if (c->out_ready) cudaEventDestroy(c->out_ready);
+    for (auto e : c->chunk_ev)
+        if (e) cudaEventDestroy(e);
     if (c->out_copied) cudaEventDestroy(c->out_copied);
     delete c;
     return QCD_OK;
@@ -679,12 +682,16 @@ extern "C" int qcd_force(qcd_ctx *c, const void *U, const void *x, const void *l
 // ---------------------------------------------------------------- profiling
 extern "C" int qcd_set_profiling(qcd_ctx *c, int on)
 {
-    if (!c) return QCD_EINVAL;
-    if (!on) {
+    if (!c || on < 0 || on > 2) return QCD_EINVAL;
+    if (on != 1) {
         int rc = collect_profile(c);
         if (rc) return rc;
     }
-    c->profiling = on != 0;
+    c->profiling = on == 1;
+    c->chunk_timing = on == 2;
+    if (on == 2)
+        for (auto &e : c->chunk_ev)
+            if (!e) QCD_CUDA_CHECK(cudaEventCreate(&e));
     return QCD_OK;
 }
 

@@ -133,6 +133,12 @@ struct qcd_ctx {
 
     // profiling
     bool profiling = false;
+    // chunk timing (qcd_set_profiling(ctx, 2)): one event pair around each
+    // queued chunk of FP32-level iterations, none around single launches;
+    // chunk_bytes sums the algorithmic bytes of the launches issued
+    bool chunk_timing = false;
+    double chunk_bytes = 0.0;
+    cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
     struct Pending {
         cudaEvent_t a, b;
         int cls;

@@ -101,10 +101,29 @@ int run_bicg(qcd_ctx *c, Level &L, SolverState *final_state)
     int queued = 0;
     int chunk = 3;
     double rr0 = -1.0;
+    // chunk timing of the FP32 level: the launches of a chunk run back to
+    // back as in any solve, one event pair around them
+    const bool timed = c->chunk_timing && L.prec == QCD_F32;
+    int it_before = 0;
     for (;;) {
+        const double by0 = c->chunk_bytes;
+        if (timed) QCD_CUDA_CHECK(cudaEventRecord(c->chunk_ev[0], c->stream));
         for (int k = 0; k < chunk; ++k) TRY(bicg_iteration(c, L));
+        if (timed) QCD_CUDA_CHECK(cudaEventRecord(c->chunk_ev[1], c->stream));
         queued += chunk;
         TRY(read_state(c, L.slot, &h));
+        if (timed) {
+            float ms = 0.f;
+            QCD_CUDA_CHECK(cudaEventElapsedTime(&ms, c->chunk_ev[0], c->chunk_ev[1]));
+            // iterations the chunk ran (the queue may overrun convergence:
+            // those launches return at once and move no data)
+            const int ran = h.iter - it_before;
+            it_before = h.iter;
+            qcd_kernel_stat &k = c->stats[QCD_K_INNER_ITER];
+            k.launches += ran;
+            k.ms += ms;
+            k.bytes += (c->chunk_bytes - by0) * ran / chunk;
+        }
         if (rr0 < 0.0) rr0 = h.rr > 0 ? h.rr : 1.0;
         if (h.done) break;
         if (queued > h.maxit + 8) {  // cannot happen: FIN_X caps at maxit

@@ -13,7 +13,7 @@ import os
 from dataclasses import dataclass, field
 
 F64, F32, F16, DF64 = 0, 1, 2, 3
-K_MULT_F64, K_MULT_F32, K_MULT_F16, K_BLAS, K_OTHER, K_DHAT_F32, K_MULT_DF64, K_BLAS_F32 = 0, 1, 2, 3, 4, 5, 6, 7
+K_MULT_F64, K_MULT_F32, K_MULT_F16, K_BLAS, K_OTHER, K_DHAT_F32, K_MULT_DF64, K_BLAS_F32, K_INNER_ITER = range(9)
 
 STATUS = {
     0: "QCD_OK", -1: "QCD_EINVAL", -2: "QCD_ECUDA", -3: "QCD_ENOMEM", -4: "QCD_ENOTCONV",
@@ -295,7 +295,9 @@ class Context:
         _check(self.lib.qcd_force(self._h, _ptr(U), _ptr(x), _ptr(lam), _ptr(G)))
 
     # ---- kernel timing
-    def set_profiling(self, on: bool):
+    def set_profiling(self, on):
+        """0 off, 1 (True) events around every launch, 2 chunk timing of the
+        FP32-level iterations (qcd_set_profiling)."""
         _check(self.lib.qcd_set_profiling(self._h, int(on)))
 
     def kernel_stats(self, cls: int) -> dict:

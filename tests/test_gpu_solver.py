@@ -336,3 +336,27 @@ def test_wilson_without_clover():
     assert info["status"] == 0
     assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
     ctx.close()
+
+
+def test_chunk_timing_counts_whole_iterations(lat8):
+    """qcd_set_profiling(ctx, 2): one event pair per queued chunk of FP32
+    iterations; the class QCD_K_INNER_ITER must count exactly the solve's
+    inner iterations, with their algorithmic bytes (two D^ with the fused
+    dots and three BLAS-1 updates: about 5088 bytes per even site), and the
+    solve must be unchanged by it."""
+    qcd = lat8["qcd"]
+    ctx = lat8["ctx"]
+    x0, i0 = solve(lat8, precision_levels=2)
+    ctx.reset_kernel_stats()
+    ctx.set_profiling(2)
+    x1, i1 = solve(lat8, precision_levels=2)
+    ctx.set_profiling(0)
+    assert np.array_equal(x0, x1)
+    st = ctx.kernel_stats(qcd.K_INNER_ITER)
+    assert st["launches"] == i1["inner_iters"][0] > 0
+    assert st["ms"] > 0
+    vh = inputs.volume(lat8["dims"]) // 2
+    per_site = st["bytes"] / st["launches"] / vh
+    assert 4800 < per_site < 5300, per_site
+    with pytest.raises(qcd.QCDError):
+        ctx.set_profiling(3)
