@@ -171,17 +171,18 @@ int tune_one(qcd_ctx *c, StencilCall s, qcd_ctx::TuneEntry *out)
     s.done = nullptr;
     // variant 1: the register cap (80 for FP32 and FP16, 128 for DF64);
     // variant 2: the hops software-pipelined (FP32 / FP16 MULT and D^
-    // halves, one right-hand side)
+    // halves, one right-hand side); the multi-RHS kernel: 0 / 1 staged words
+    // in shared memory, 2 / 3 in tensor memory, 1 / 3 with the 80-register cap
     const bool low = s.prec == QCD_F32 || s.prec == QCD_F16;
     const bool pipe = low && s.nrhs == 1 && (s.mode == M_MULT || s.mode == M_DHAT || s.mode == M_FULL);
-    const int nv = pipe ? 3 : (low || s.prec == QCD_DF64) ? 2 : 1;
+    const bool mr = is_mrhs(s);
+    const int nv = mr ? 4 : pipe ? 3 : (low || s.prec == QCD_DF64) ? 2 : 1;
     // sites per block; for the multi-RHS kernel the right-hand sides per block
     // (all, a half, a third, a quarter)
     const int bxs1[] = {64, 128, 256}, bxsn[] = {32, 64};
     int bxst[4], nt = 0;
     for (int d : {1, 2, 3, 4})
         if (s.nrhs % d == 0) bxst[nt++] = s.nrhs / d;
-    const bool mr = is_mrhs(s);
     const int *bxs = mr ? bxst : s.nrhs > 1 ? bxsn : bxs1;
     const int nbx = mr ? nt : s.nrhs > 1 ? 2 : 3;
     qcd_ctx::TuneEntry best{0, 128, 1e30};
@@ -220,7 +221,7 @@ int autotune(qcd_ctx *c, const char *cache_path)
         {QCD_F64, M_MULT, R_NONE, 1},  {QCD_F64, M_DHAT, R_DOT_AUX, 1}, {QCD_F64, M_DHAT, R_OMEGA, 1},
         {QCD_F64, M_SRC, R_NONE, 1},   {QCD_F64, M_FULL, R_NORM, 1},    {QCD_F64, M_DHAT, R_NORM, 1},
         {QCD_F32, M_MULT, R_NONE, 1},  {QCD_F32, M_DHAT, R_DOT_AUX, 1}, {QCD_F32, M_DHAT, R_OMEGA, 1},
-        {QCD_F32, M_HOP, R_NONE, 1},   {QCD_F32, M_MULT, R_NONE, 12},
+        {QCD_F32, M_HOP, R_NONE, 1},   {QCD_F32, M_MULT, R_NONE, 12},  {QCD_F32, M_HOP, R_NONE, 12},
         {QCD_F16, M_MULT, R_NONE, 1},  {QCD_F16, M_DHAT, R_DOT_AUX, 1}, {QCD_F16, M_DHAT, R_OMEGA, 1},
         {QCD_F16, M_MULT, R_NONE, 12},
         {QCD_DF64, M_MULT, R_NONE, 1}, {QCD_DF64, M_DHAT, R_DOT_AUX, 1}, {QCD_DF64, M_DHAT, R_OMEGA, 1},

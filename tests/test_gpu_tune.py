@@ -26,14 +26,14 @@ def test_autotune_cache_and_parity(tmp_path):
     ctx.autotune(cache)
     entries = ctx.tune_info()
     assert len(entries) >= 15
-    def mrhs(e):  # the shared-memory multi-RHS kernel: FP32 hopping / MULT, several RHS
+    def mrhs(e):  # the staged multi-RHS kernel: FP32 hopping / MULT, several RHS
         return e["prec"] == 1 and e["nrhs"] > 1 and e["red"] == 0 and e["mode"] in (0, 1)
 
     def piped(e):  # FP32 / FP16 single-RHS MULT and D^ halves: also the pipelined-hop kernel
         return e["prec"] in (1, 2) and e["nrhs"] == 1 and e["mode"] in (1, 2, 4)
 
     for e in entries:
-        assert e["variant"] in ((0, 1, 2) if piped(e) else (0, 1))
+        assert e["variant"] in ((0, 1, 2) if piped(e) else (0, 1, 2, 3) if mrhs(e) else (0, 1))
         if mrhs(e):  # threads = right-hand sides per block, a divisor of nrhs
             assert e["nrhs"] % e["threads"] == 0
         else:
@@ -93,8 +93,8 @@ def test_forced_launch_shapes_keep_parity(tmp_path, cap):
     for k, (variant, bx, us) in list(data.items()):
         key = int(k.rsplit("|", 1)[1])
         prec, mode, red, nrhs = key & 3, (key >> 2) & 7, (key >> 5) & 3, key >> 8
-        if prec == 1 and nrhs > 1 and red == 0 and mode in (0, 1):  # multi-RHS kernel, its three variants
-            data[k] = [{1: 1, 2: 0}[cap], 4, us]
+        if prec == 1 and nrhs > 1 and red == 0 and mode in (0, 1):  # multi-RHS kernel: tensor memory, tile 4
+            data[k] = [{1: 3, 2: 2}[cap], 4, us]
         elif prec in (1, 2) and nrhs == 1 and mode in (1, 2, 4):
             data[k] = [cap, 64, us]
         else:
@@ -146,4 +146,66 @@ def test_forced_launch_shapes_keep_parity(tmp_path, cap):
         info = ctx.solve(bd, x, tol=1e-12, precision_levels=levels, eo_hermitian=herm)
         assert info["status"] == 0
         assert oracle.true_residual(dims, t_bc, U, F, kappa, b, x.cpu().numpy()) <= 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("tile", [12, 4])
+def test_multi_rhs_variants_bit_exact(tmp_path, variant, tile):
+    """The multi-RHS kernel with its staged links and clover read from shared
+    memory (variants 0, 1) or tensor memory (2, 3), each with and without the
+    register cap, at a tile of 12 and of 4 right-hand sides: every right-hand
+    side of the FP32 MULT and hopping term, plain and daggered, equals the
+    single-RHS kernel's result to the bit, on a lattice with a ragged last
+    site block, and the MULT matches the oracle."""
+    from paper_1709_08785_gb300 import qcd
+
+    dims, kappa, csw, t_bc = (6, 2, 4, 10), 0.124, 1.6, -1  # Vh = 240: ragged blocks
+    U = inputs.random_gauge(dims, 0.25, 98)
+    cache = str(tmp_path / "tune.json")
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    ctx.autotune(cache)
+    data = json.load(open(cache))
+    forced = 0
+    for k, (v, bx, us) in list(data.items()):
+        key = int(k.rsplit("|", 1)[1])
+        prec, mode, red, nrhs = key & 3, (key >> 2) & 7, (key >> 5) & 3, key >> 8
+        if prec == 1 and nrhs == 12 and red == 0 and mode in (0, 1):
+            data[k] = [variant, tile, us]
+            forced += 1
+    assert forced == 2  # the hopping term and the MULT
+    with open(cache, "w") as f:  # the cache's own layout: one entry per line
+        f.write("{\n" + ",\n".join('  "%s": [%d, %d, %.3f]' % (k, *e) for k, e in data.items()) + "\n}\n")
+    ctx.close()
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    ctx.autotune(cache)
+    got_v = {(e["mode"], e["variant"], e["threads"]) for e in ctx.tune_info() if e["nrhs"] == 12 and e["prec"] == 1}
+    assert got_v == {(0, variant, tile), (1, variant, tile)}
+    F = oracle.clover_field(dims, U, kappa, csw)
+    Fi = oracle.invert_sites(F)
+    Vh = inputs.volume(dims) // 2
+    vs = np.stack([inputs.gaussian_source(dims, 100 + k)[:Vh] for k in range(12)])
+    inp = torch.from_numpy(vs).to(torch.complex64).cuda()
+
+    def launch(fn, x, n):
+        out = torch.zeros_like(x)
+        fn(out, x, n)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    for dag in (False, True):
+        for op in ("mult_eo", "dslash_eo"):
+            f = getattr(ctx, op)
+            many = launch(lambda o, x, n: f(o, x, 1, dag, 1, n), inp, 12)
+            for k in range(12):
+                one = launch(lambda o, x, n: f(o, x, 1, dag, 1, n), inp[k].contiguous(), 1)
+                assert np.array_equal(many[k], one), (op, dag, k)
+                if op == "mult_eo" and not dag:
+                    wk = oracle.mult(dims, t_bc, U, Fi, 1, vs[k])
+                    gk = many[k].astype(np.complex128)
+                    assert np.linalg.norm(gk - wk) / np.linalg.norm(wk) < 2e-6, k
     ctx.close()
