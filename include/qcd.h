@@ -326,9 +326,7 @@ int qcd_autotune(qcd_ctx *ctx, const char *cache_path);
  * compiler's register budget, 1 capped at 80 registers (128 for QCD_DF64),
  * 2 the FP32 / FP16 kernel whose hops are software-pipelined (the next
  * hop's neighbour spinor and link loaded before the current hop computes);
- * for the FP32 multi-RHS MULT and hopping term 0 / 1 the staged links and
- * clover read from shared memory, 2 / 3 from tensor memory, 1 / 3 capped at
- * 80 registers; threads per block along the sites, or
+ * threads per block along the sites, or
  * right-hand sides per block for the multi-RHS kernel; microseconds per
  * launch); returns the number of entries held. Any output pointer may be
  * NULL. */

@@ -23,7 +23,8 @@ int dispatch_f64(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 bl
 int dispatch_f32(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int v);
 int dispatch_f16(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int v);
 int dispatch_df64(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int v);
-int launch_mrhs(const StencilCall &sc, const StencilArgs &A, int nrhs, cudaStream_t s, int variant, int tile);
+int launch_mrhs(const StencilCall &sc, const StencilArgs &A, int nrhs, cudaStream_t s, int variant, int tile,
+                int num_sms);
 
 // Algorithmic bytes per output site of one stencil launch (each input read
 // once, the output written once), by precision: spinor, link, clover.
@@ -146,7 +147,7 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
     A.skip = prof.flag;
     int rc;
     const int rv = variant;
-    if (is_mrhs(sc)) rc = launch_mrhs(sc, A, nrhs, c->stream, rv, bx);
+    if (is_mrhs(sc)) rc = launch_mrhs(sc, A, nrhs, c->stream, rv, bx, c->num_sms);
     else if (p == QCD_F64) rc = dispatch_f64(sc, A, grid, block, c->stream, rv);
     else if (p == QCD_F32) rc = dispatch_f32(sc, A, grid, block, c->stream, rv);
     else if (p == QCD_DF64) rc = dispatch_df64(sc, A, grid, block, c->stream, rv);

@@ -113,6 +113,63 @@ __device__ __forceinline__ void expand_w(Spinor<T> &acc, const cx<T> g[2][3], T 
     }
 }
 
+// ---- packed FP32 pairs -------------------------------------------------------
+// Blackwell issues an FP32 operation on a register pair as one instruction
+// (two lanes, each rounded as the scalar fmaf / add / mul).  The multi-RHS
+// hops use it on the two spin rows of a half spinor: the link products of
+// rows 0 and 1 share every link element, and the accumulator's upper spins
+// pair as {s0, s1}, its lower ones as {s3, s2} -- the order in which the x, y
+// and t expansions keep their lanes.  Each lane repeats the scalar forms'
+// operations in their order (a negated operand moved to the other factor,
+// which is exact), so the results equal theirs to the bit.  (In the
+// single-RHS FP16 hops the pairs cost more registers than they save issue
+// slots: no faster, measured.)
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// project's rows as the pair {h0, h1}; mu = t, S = +1 feeds the lower pair
+// {s3, s2} and is ordered {h1, h0}
+template <int MU, int S>
+__device__ __forceinline__ void project_pair(const Spinor<float> &psi, float2 Hr[3], float2 Hi[3])
+{
+    cx<float> h[2][3];
+    project<MU, S>(psi, h);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int a0 = (MU == 3 && S > 0) ? 1 : 0;
+        Hr[c] = make_float2(h[a0][c].r, h[1 - a0][c].r);
+        Hi[c] = make_float2(h[a0][c].i, h[1 - a0][c].i);
+    }
+}
+
+// G = U H (BWD = 0) or U^dag H (BWD = 1) on the row pair H, u(k) the link
+// element k = 3 i + j as {re, im}; colour_mul's fma_ / fmac_ lane by lane
+template <int BWD, class LinkAt>
+__device__ __forceinline__ void colour_mul_pair(const LinkAt &u, const float2 Hr[3], const float2 Hi[3], float2 Gr[3],
+                                                float2 Gi[3])
+{
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 N[3];  // (-u_im) x = u_im (-x): -H_im for U, -H_re for U^dag
+#pragma unroll
+    for (int j = 0; j < 3; ++j) N[j] = pmul(BWD ? Hr[j] : Hi[j], m1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float2 sr = make_float2(0.f, 0.f), si = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float2 e = u(BWD ? 3 * j + i : 3 * i + j);
+            const float2 ur = make_float2(e.x, e.x), ui = make_float2(e.y, e.y);
+            sr = pfma(ur, Hr[j], sr);
+            sr = pfma(ui, BWD ? Hi[j] : N[j], sr);
+            si = pfma(ur, Hi[j], si);
+            si = pfma(ui, BWD ? N[j] : Hr[j], si);
+        }
+        Gr[i] = sr;
+        Gi[i] = si;
+    }
+}
+
 // complex double-float products gathered in compensated accumulators
 // (dacc): a += x*y, a += conj(x)*y
 __device__ __forceinline__ void cdacc_fma(dacc &ar, dacc &ai, const cx<df> &x, const cx<df> &y)

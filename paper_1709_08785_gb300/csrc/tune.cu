@@ -171,12 +171,11 @@ int tune_one(qcd_ctx *c, StencilCall s, qcd_ctx::TuneEntry *out)
     s.done = nullptr;
     // variant 1: the register cap (80 for FP32 and FP16, 128 for DF64);
     // variant 2: the hops software-pipelined (FP32 / FP16 MULT and D^
-    // halves, one right-hand side); the multi-RHS kernel: 0 / 1 staged words
-    // in shared memory, 2 / 3 in tensor memory, 1 / 3 with the 80-register cap
+    // halves, one right-hand side)
     const bool low = s.prec == QCD_F32 || s.prec == QCD_F16;
     const bool pipe = low && s.nrhs == 1 && (s.mode == M_MULT || s.mode == M_DHAT || s.mode == M_FULL);
     const bool mr = is_mrhs(s);
-    const int nv = mr ? 4 : pipe ? 3 : (low || s.prec == QCD_DF64) ? 2 : 1;
+    const int nv = mr ? 2 : pipe ? 3 : (low || s.prec == QCD_DF64) ? 2 : 1;
     // sites per block; for the multi-RHS kernel the right-hand sides per block
     // (all, a half, a third, a quarter)
     const int bxs1[] = {64, 128, 256}, bxsn[] = {32, 64};
