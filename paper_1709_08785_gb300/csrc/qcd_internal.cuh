@@ -443,19 +443,17 @@ struct Prec<QCD_F16> {
             }
         }
     }
-    // the stored halves unscaled; returns the site's norm (psi = norm * halves)
-    static __device__ __forceinline__ float load_raw(const SpinorPtr &v, int cb, Spinor<T> &s)
+    // the 12 stored half2 words as loaded; returns the site's norm
+    static __device__ __forceinline__ float load_half(const SpinorPtr &v, int cb, unsigned w[12])
     {
         const uint4 *p = (const uint4 *)v.p;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            uint4 q = __ldg(p + soa(cb, 3, k));
-            unsigned w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                int c = 4 * k + j;
-                s.s[c / 3][c % 3] = h2c(u2h(w[j]));
-            }
+            const uint4 q = __ldg(p + soa(cb, 3, k));
+            w[4 * k] = q.x;
+            w[4 * k + 1] = q.y;
+            w[4 * k + 2] = q.z;
+            w[4 * k + 3] = q.w;
         }
         return __ldg(v.norm + cb);
     }

@@ -35,6 +35,62 @@ __device__ __forceinline__ void project(const Spinor<T> &p, cx<T> h[2][3])
     }
 }
 
+// ---- projection of a stored FP16 spinor -------------------------------------
+// The 12 half2 words (re, im) of a neighbour spinor as loaded, component
+// 3 a + i in word 3 a + i, unscaled (the site's norm goes into the expansion).
+struct HalfSpinor {
+    unsigned w[12];
+};
+__device__ __forceinline__ unsigned short hre(unsigned w) { return (unsigned short)(w & 0xffffu); }
+__device__ __forceinline__ unsigned short him(unsigned w) { return (unsigned short)(w >> 16); }
+__device__ __forceinline__ float hf(unsigned short h) { return __half2float(__ushort_as_half(h)); }
+// a + b and a - b with the half a widened inside the add (exact), one rounding
+// as in float(a) +- b
+__device__ __forceinline__ float hadd(unsigned short a, float b)
+{
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float hsub(unsigned short a, float b)
+{
+    float d;
+    asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(b));
+    return d;
+}
+
+// project<MU, S> on the stored halves: each projected real is the first
+// spin's half plus or minus the second spin's half widened, the same single
+// rounding as the FP32 form, one conversion fewer
+template <int MU, int S>
+__device__ __forceinline__ void project_h(const HalfSpinor &p, cx<float> h[2][3])
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const unsigned p0 = p.w[i], p1 = p.w[3 + i], p2 = p.w[6 + i], p3 = p.w[9 + i];
+        if (MU == 0) {  // h0 = p0 +- i p3, h1 = p1 +- i p2
+            h[0][i] = S > 0 ? mk(hsub(hre(p0), hf(him(p3))), hadd(him(p0), hf(hre(p3))))
+                            : mk(hadd(hre(p0), hf(him(p3))), hsub(him(p0), hf(hre(p3))));
+            h[1][i] = S > 0 ? mk(hsub(hre(p1), hf(him(p2))), hadd(him(p1), hf(hre(p2))))
+                            : mk(hadd(hre(p1), hf(him(p2))), hsub(him(p1), hf(hre(p2))));
+        } else if (MU == 1) {  // h0 = p0 +- p3, h1 = p1 -+ p2
+            h[0][i] = S > 0 ? mk(hadd(hre(p0), hf(hre(p3))), hadd(him(p0), hf(him(p3))))
+                            : mk(hsub(hre(p0), hf(hre(p3))), hsub(him(p0), hf(him(p3))));
+            h[1][i] = S > 0 ? mk(hsub(hre(p1), hf(hre(p2))), hsub(him(p1), hf(him(p2))))
+                            : mk(hadd(hre(p1), hf(hre(p2))), hadd(him(p1), hf(him(p2))));
+        } else if (MU == 2) {  // h0 = p0 +- i p2, h1 = p1 -+ i p3
+            h[0][i] = S > 0 ? mk(hsub(hre(p0), hf(him(p2))), hadd(him(p0), hf(hre(p2))))
+                            : mk(hadd(hre(p0), hf(him(p2))), hsub(him(p0), hf(hre(p2))));
+            h[1][i] = S > 0 ? mk(hadd(hre(p1), hf(him(p3))), hsub(him(p1), hf(hre(p3))))
+                            : mk(hsub(hre(p1), hf(him(p3))), hadd(him(p1), hf(hre(p3))));
+        } else {
+            const unsigned a = S > 0 ? p2 : p0, b = S > 0 ? p3 : p1;
+            h[0][i] = mk(hf(hre(a)), hf(him(a)));
+            h[1][i] = mk(hf(hre(b)), hf(him(b)));
+        }
+    }
+}
+
 // 2 a, exactly
 template <class T>
 __device__ __forceinline__ cx<T> twice(cx<T> a)
@@ -246,8 +302,9 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const LinkF &links, const
         cx<T> h[2][3], q[2][3];
         Link<T> L;
         if constexpr (P == QCD_F16) {  // the neighbour's norm and the boundary sign go into the accumulation
-            const T w = Prec<P>::load_raw(in, nb, psi);
-            project<MU, SF>(psi, h);
+            HalfSpinor hs;
+            const T w = Prec<P>::load_half(in, nb, hs.w);
+            project_h<MU, SF>(hs, h);
             links.template load<MU, 0>(nb, L);
             colour_mul<false>(L, h, q);
             expand_w<MU, SF>(acc, q, flip ? -w : w);
@@ -272,8 +329,9 @@ __device__ __forceinline__ void hop_dir(const Geom &g, const LinkF &links, const
         cx<T> h[2][3], q[2][3];
         Link<T> L;
         if constexpr (P == QCD_F16) {
-            const T w = Prec<P>::load_raw(in, nb, psi);
-            project<MU, -SF>(psi, h);
+            HalfSpinor hs;
+            const T w = Prec<P>::load_half(in, nb, hs.w);
+            project_h<MU, -SF>(hs, h);
             links.template load<MU, 1>(nb, L);
             colour_mul<true>(L, h, q);
             expand_w<MU, -SF>(acc, q, flip ? -w : w);
@@ -388,17 +446,10 @@ __device__ __forceinline__ void raw_hop_apply(const Geom &g, const int c[4], con
         }
         expand<MU, S>(acc, q);
     } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const unsigned w[4] = {R.s[k].x, R.s[k].y, R.s[k].z, R.s[k].w};
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int cc = 4 * k + j;
-                psi.s[cc / 3][cc % 3] = h2c(u2h(w[j]));
-            }
-        }
+        const HalfSpinor hs{{R.s[0].x, R.s[0].y, R.s[0].z, R.s[0].w, R.s[1].x, R.s[1].y, R.s[1].z, R.s[1].w, R.s[2].x,
+                             R.s[2].y, R.s[2].z, R.s[2].w}};
         Prec<P>::unpack_link(R.la, R.lb, L);
-        project<MU, S>(psi, h);
+        project_h<MU, S>(hs, h);
         colour_mul<BWD == 1>(L, h, q);
         expand_w<MU, S>(acc, q, flip ? -R.n : R.n);  // the neighbour's norm and the boundary sign
     }
