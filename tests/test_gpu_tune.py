@@ -208,3 +208,66 @@ def test_multi_rhs_variants_bit_exact(tmp_path, variant, tile):
                     gk = many[k].astype(np.complex128)
                     assert np.linalg.norm(gk - wk) / np.linalg.norm(wk) < 2e-6, k
     ctx.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("tile", [12, 4])
+def test_multi_rhs_resident_loop_bit_exact(tmp_path, variant, tile):
+    """The multi-RHS kernel's resident blocks walk several site blocks each
+    (16^3x32: 2048 site blocks, two blocks per SM), copying the next one in
+    while they compute: every right-hand side of the FP32 MULT and hopping
+    term, plain and daggered, equals the single-RHS kernel's result to the
+    bit, and the MULT of the first matches the oracle at sampled sites."""
+    from paper_1709_08785_gb300 import qcd
+
+    dims, kappa, csw, t_bc = (16, 16, 16, 32), 0.124, 1.6, -1
+    U = inputs.random_gauge(dims, 0.25, 99)
+    cache = str(tmp_path / "tune.json")
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    ctx.autotune(cache)
+    data = json.load(open(cache))
+    for k, (v, bx, us) in list(data.items()):
+        key = int(k.rsplit("|", 1)[1])
+        prec, mode, red, nrhs = key & 3, (key >> 2) & 7, (key >> 5) & 3, key >> 8
+        if prec == 1 and nrhs == 12 and red == 0 and mode in (0, 1):
+            data[k] = [variant, tile, us]
+    with open(cache, "w") as f:  # the cache's own layout: one entry per line
+        f.write("{\n" + ",\n".join('  "%s": [%d, %d, %.3f]' % (k, *e) for k, e in data.items()) + "\n}\n")
+    ctx.close()
+    ctx = qcd.Context(dims, t_bc)
+    ctx.gauge_load(torch.from_numpy(U).cuda())
+    ctx.clover_build(kappa, csw)
+    ctx.autotune(cache)
+    got_v = {(e["mode"], e["variant"], e["threads"]) for e in ctx.tune_info() if e["nrhs"] == 12 and e["prec"] == 1}
+    assert got_v == {(0, variant, tile), (1, variant, tile)}
+    Vh = inputs.volume(dims) // 2
+    assert Vh // 32 > 2 * 152 * 2  # several site blocks per resident block
+    vs = np.stack([inputs.gaussian_source(dims, 110 + k)[:Vh] for k in range(12)])
+    inp = torch.from_numpy(vs).to(torch.complex64).cuda()
+
+    def launch(fn, x, n):
+        out = torch.zeros_like(x)
+        fn(out, x, n)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    for dag in (False, True):
+        for op in ("mult_eo", "dslash_eo"):
+            f = getattr(ctx, op)
+            many = launch(lambda o, x, n: f(o, x, 1, dag, 1, n), inp, 12)
+            for k in range(12):
+                one = launch(lambda o, x, n: f(o, x, 1, dag, 1, n), inp[k].contiguous(), 1)
+                assert np.array_equal(many[k], one), (op, dag, k)
+            if op == "mult_eo" and not dag:
+                rng = np.random.default_rng(7)
+                cbs = np.concatenate([rng.choice(Vh - 64, 56, replace=False), np.arange(Vh - 8, Vh)])
+                v_full = oracle.half_to_full(dims, 0, vs[0])
+                sites = oracle.site_of_cb(dims, 1, cbs)
+                h = oracle.hop_sites(dims, t_bc, U, v_full, sites)
+                F = oracle.clover_sites(dims, U, kappa, csw, sites)
+                want = np.linalg.solve(F, h.reshape(len(cbs), 12, 1)).reshape(len(cbs), 4, 3)
+                got = many[0].reshape(Vh, 4, 3)[cbs].astype(np.complex128)
+                assert np.linalg.norm((got - want).ravel()) / np.linalg.norm(want.ravel()) < 2e-6
+    ctx.close()
