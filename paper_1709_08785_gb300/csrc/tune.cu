@@ -104,11 +104,15 @@ int write_cache(const char *path, const Cache &m)
 }
 
 // scratch: nrhs input and nrhs output vectors of one precision
-int tune_buffers(qcd_ctx *c, int prec, int nrhs, HVec *in, HVec *out)
+// the candidates' vectors: in, out and, for one right-hand side, the
+// epilogue vector y and the dot operand aux as buffers of their own, so
+// that the D^ halves move the bytes they move in a solve
+int tune_buffers(qcd_ctx *c, int prec, int nrhs, HVec *in, HVec *out, HVec *y, HVec *aux)
 {
     const size_t hb = hvec_bytes(c->g, prec);
     const size_t nb = (size_t)c->g.Vh_pad * sizeof(float);
-    const size_t need = 2 * nrhs * (hb + nb);
+    const int nv = nrhs == 1 ? 4 : 2;
+    const size_t need = nv * nrhs * (hb + nb);
     if (c->tune_bytes < need) {
         if (c->tune_buf) {
             cudaStreamSynchronize(c->stream);
@@ -123,12 +127,16 @@ int tune_buffers(qcd_ctx *c, int prec, int nrhs, HVec *in, HVec *out)
         c->tune_bytes = need;
     }
     char *base = (char *)c->tune_buf;
-    in->prec = out->prec = prec;
-    in->p = base;
-    out->p = base + nrhs * hb;
-    in->norm = (float *)(base + 2 * nrhs * hb);
-    out->norm = (float *)(base + 2 * nrhs * hb + nrhs * nb);
-    return fill_pattern(c, prec, *in, nrhs, hvec_elems(c->g, prec), 11);
+    HVec *v[4] = {in, out, y, aux};
+    for (int k = 0; k < 4; ++k) {
+        const int j = k < nv ? k : 0;  // several right-hand sides: y and aux alias in
+        v[k]->prec = prec;
+        v[k]->p = base + j * nrhs * hb;
+        v[k]->norm = (float *)(base + nv * nrhs * hb + j * nrhs * nb);
+    }
+    int rc = fill_pattern(c, prec, *in, nrhs, hvec_elems(c->g, prec), 11);
+    for (int k = 2; k < nv && rc == QCD_OK; ++k) rc = fill_pattern(c, prec, *v[k], nrhs, hvec_elems(c->g, prec), 11 + k);
+    return rc;
 }
 
 int time_candidate(qcd_ctx *c, const StencilCall &s, double *us)
@@ -157,14 +165,14 @@ int time_candidate(qcd_ctx *c, const StencilCall &s, double *us)
 
 int tune_one(qcd_ctx *c, StencilCall s, qcd_ctx::TuneEntry *out)
 {
-    HVec in, o;
-    int rc = tune_buffers(c, s.prec, s.nrhs, &in, &o);
+    HVec in, o, y, aux;
+    int rc = tune_buffers(c, s.prec, s.nrhs, &in, &o, &y, &aux);
     if (rc) return rc;
     s.in = in;
     s.out = o;
-    s.y = in;
-    s.aux = in;
-    s.z = in;
+    s.y = y;
+    s.aux = aux;
+    s.z = aux;
     s.rhs_stride = hvec_elems(c->g, s.prec);
     s.norm_stride = (size_t)c->g.Vh_pad;
     s.red_args = RedArgs{c->partials, c->counters, c->states + ST_TUNE, FIN_NONE};
