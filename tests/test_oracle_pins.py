@@ -14,6 +14,8 @@ of them:
 * the gamma5-hermitian even-odd operator S_ee: exact gamma5-hermiticity,
   S_ee = F_ee D^_ee, its source, and a dense solve on 4^4;
 * a dense brute-force matrix on a 2^4 lattice (every hop lands twice);
+* the even-odd pieces: the half / full embedding by coordinate parity, the
+  half-lattice hopping term as the full one restricted, MULT from D;
 * the clover inverse, the even-odd identities (Eqs. 5-9), dense LU solves
   against BiCGStab (Algs. 1-2), and finite differences for the gradient.
 """
@@ -317,6 +319,68 @@ def test_even_odd_identities(t_bc):
     assert np.max(np.abs(oracle.full_to_half(dims, 1, r))) < 1e-12
     re = oracle.site_apply(oracle.field_to_half(dims, 0, F), bh - oracle.dhat(dims, t_bc, U, Fi, kappa, ye))
     assert rel(oracle.full_to_half(dims, 0, r), re) < 1e-13
+
+
+# ------------------------------------------------------------- even-odd pieces
+def _parity_of_lex(dims, lex):
+    """(x + y + z + t) mod 2 of lexicographic sites, x fastest (Sec. II-B)."""
+    lex = np.asarray(lex)
+    c, r = [], lex
+    for L in dims:
+        c.append(r % L)
+        r = r // L
+    return (c[0] + c[1] + c[2] + c[3]) % 2
+
+
+@pytest.mark.parametrize("parity", [0, 1])
+def test_half_full_embedding(parity):
+    """A half-lattice vector lands on the sites of its parity (coordinate sum
+    mod 2), in cb order, zero elsewhere, and comes back unchanged."""
+    dims = (4, 2, 6, 4)
+    Vh = inputs.volume(dims) // 2
+    v = inputs.gaussian_source(dims, 40 + parity)[:Vh]
+    full = oracle.half_to_full(dims, parity, v)
+    lex = oracle.site_of_cb(dims, parity, np.arange(Vh))
+    assert np.all(_parity_of_lex(dims, lex) == parity)
+    assert np.all(np.diff(lex) > 0)  # cb order is lexicographic order within the parity
+    assert np.array_equal(full[lex], v)
+    other = np.setdiff1d(np.arange(inputs.volume(dims)), lex)
+    assert np.all(_parity_of_lex(dims, other) == 1 - parity)
+    assert not np.any(full[other])
+    assert np.array_equal(oracle.full_to_half(dims, parity, full), v)
+
+
+@pytest.mark.parametrize("t_bc", [1, -1])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_hop_eo_is_the_full_hopping_restricted(t_bc, dagger):
+    """H_{p,1-p} on half vectors equals the full-lattice H (pinned above by the
+    free field, the dense 2^4 matrix and gamma5-hermiticity) applied to the
+    embedded vector and read on parity p."""
+    dims = (4, 4, 2, 6)
+    U = inputs.random_gauge(dims, 0.25, 42)
+    Vh = inputs.volume(dims) // 2
+    v = inputs.gaussian_source(dims, 43)[:Vh]
+    for p in (0, 1):
+        want = oracle.full_to_half(dims, p, oracle.hopping(dims, t_bc, U, oracle.half_to_full(dims, 1 - p, v), dagger))
+        assert rel(oracle.hop_eo(dims, t_bc, U, p, v, dagger), want) < 1e-15
+
+
+@pytest.mark.parametrize("t_bc", [1, -1])
+def test_mult_from_the_dirac_operator(t_bc):
+    """MULT = F_pp^-1 H_{p,1-p} (Sec. II-B): for v on parity 1-p only, the
+    Dirac operator gives (D v)_p = -kappa (H v)_p (F is site-diagonal), so
+    MULT v = -F_pp^-1 (D v)_p / kappa, with D and F^-1 pinned above."""
+    dims = (4, 2, 4, 6)
+    kappa, csw = 0.124, 1.6
+    U = inputs.random_gauge(dims, 0.25, 44)
+    F = oracle.clover_field(dims, U, kappa, csw)
+    Fi = oracle.invert_sites(F)
+    Vh = inputs.volume(dims) // 2
+    v = inputs.gaussian_source(dims, 45)[:Vh]
+    for p in (0, 1):
+        dv = oracle.dirac(dims, t_bc, U, F, kappa, oracle.half_to_full(dims, 1 - p, v))
+        want = -oracle.site_apply(oracle.field_to_half(dims, p, Fi), oracle.full_to_half(dims, p, dv)) / kappa
+        assert rel(oracle.mult(dims, t_bc, U, Fi, p, v), want) < 1e-14
 
 
 # ------------------------------------------------------------- P8 solvers
