@@ -34,9 +34,10 @@ namespace qcd {
 //             word 128 + 2 d + {re, im}, element 8 (d = 2 mu + bwd)
 //   clover    word 144 + 2 i + {+, -}, diagonal i = 0..5 of the two blocks
 //             word 160 + 4 k + {re+, re-, im+, im-}, off-diagonal k = 0..14
-//             word 224 + 2 k + {-im+, -im-}
-// each times 1/2 for the clover.
-constexpr int MR_COLS = 256;  // staged words per site
+// each times 1/2 for the clover (the negated imaginary parts the FP32-pair
+// FMAs need are formed in registers: shared-memory reads, not arithmetic,
+// bound this kernel).
+constexpr int MR_COLS = 220;  // staged words per site
 constexpr int MR_GRP = MR_COLS / 4;
 constexpr int MR_NB = 8 * SB;  // int [dir][site]
 constexpr size_t MR_BYTES = (size_t)(MR_GRP * SB + 8 * 3 * SB + 18 * SB) * sizeof(float4) + 2 * (MR_NB + SB) * sizeof(int);
@@ -158,19 +159,17 @@ __device__ __forceinline__ void herm6_pair(const Cols &cols, const float2 Xr[6],
         }
     }
     // off-diagonal k = (i, j), i = 1..5, j < i, row by row; four at a time
-    float o[16], n[8];
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float o[16];
     int k = 0;
 #pragma unroll
     for (int i = 1; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j < i; ++j) {
-            if ((k & 3) == 0) {
-                cols.get<16>(160 + 4 * k, o);
-                cols.get<8>(224 + 2 * k, n);
-                    }
+            if ((k & 3) == 0) cols.get<16>(160 + 4 * k, o);
             const int kk = k & 3;
             const float2 orr = make_float2(o[4 * kk], o[4 * kk + 1]), oi = make_float2(o[4 * kk + 2], o[4 * kk + 3]);
-            const float2 noi = make_float2(n[2 * kk], n[2 * kk + 1]);
+            const float2 noi = pmul(oi, m1);  // -im, exact
             // y_i += A_ij x_j
             Yr[i] = pfma(orr, Xr[j], Yr[i]);
             Yr[i] = pfma(noi, Xi[j], Yr[i]);
@@ -240,7 +239,7 @@ __device__ __forceinline__ void mrhs_prefetch(const StencilArgs &A, int cb0, flo
 }
 
 // the raw words to the staged layout: links rebuilt to 18 reals, the two
-// clover blocks in lane pairs, times 1/2, with the negated imaginary parts
+// clover blocks in lane pairs, times 1/2
 template <bool CLOVER>
 __device__ __forceinline__ void mrhs_unpack(const float4 *raw_l, const float4 *raw_c, float4 *s_col, int tid, int nthr)
 {
@@ -275,10 +274,6 @@ __device__ __forceinline__ void mrhs_unpack(const float4 *raw_l, const float4 *r
                     const int o = (r - 6) >> 1, im = (r - 6) & 1;
                     at(160 + 4 * o + 2 * im, l) = pp;
                     at(161 + 4 * o + 2 * im, l) = mm;
-                    if (im) {
-                        at(224 + 2 * o, l) = -pp;
-                        at(225 + 2 * o, l) = -mm;
-                    }
                 }
             }
         }
