@@ -5,7 +5,8 @@
                           solve beside the two-level and FP64-only solves, and the
                           stencil bandwidths at that size
   python bench_suite.py --workload point_sources  32^3x64: the 12-RHS Dslash against 12
-                          single launches, and the 12 point-source solves
+                          single launches, and the 12 point-source solves one after
+                          another and in lockstep (qcd_solve_multi)
   python bench_suite.py --workload batched        48 independent solves on lattices from
                           {8^4, 12^3x24, 16^3x32, 20^3x40}, tol 1e-10: one batched
                           persistent-kernel run against the same problems one by one
@@ -122,6 +123,27 @@ def w_point_sources(args):
         res.append(info["true_resid"])
         outer.append(info["outer_iters"])
     out["solves"] = {"sequential_s": round(seq, 4), "max_true_resid": max(res), "outer_iters": outer}
+    # the same 12 solves in lockstep (qcd_solve_multi: the FP32 iterations
+    # through the 12-RHS MULT), best of 3 after one untimed run; every column
+    # equals its sequential solution to the bit
+    B = torch.from_numpy(P).cuda()
+    Xm = torch.zeros_like(B)
+    ctx.solve_multi(B, Xm, tol=tol, opts=qcd.default_opts(precision_levels=2))
+    best, infos = None, None
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = ctx.solve_multi(B, Xm, tol=tol, opts=qcd.default_opts(precision_levels=2))
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        best = t if best is None else min(best, t)
+    out["solves"]["lockstep_s"] = round(best, 4)
+    out["solves"]["lockstep_speedup"] = round(seq / best, 3)
+    out["solves"]["lockstep_max_true_resid"] = max(i["true_resid"] for i in infos)
+    out["solves"]["lockstep_equals_sequential"] = bool(torch.equal(Xm, X))
+    del B, Xm
     # the pion two-point function of the 12-column propagator
     ctx.pion_correlator(X, 12)
     torch.cuda.synchronize()

@@ -225,6 +225,27 @@ void qcd_solve_opts_default(qcd_solve_opts *opts);
 int qcd_solve(qcd_ctx *ctx, const void *b, void *x, double tol, const qcd_solve_opts *opts,
               qcd_solve_info *info);
 
+/* Lockstep multi-RHS solves: nrhs systems D x_r = b_r on the context's gauge
+ * field (e.g. the 12 spin-colour point sources of a propagator), each to
+ * ||b_r - D x_r|| / ||b_r|| <= tol.  The nested scheme of qcd_solve (Alg. 1
+ * around Alg. 2, Eqs. 5-7) runs for all right-hand sides together: every
+ * FP32 iteration applies D^_ee (Eq. 8) to all of them at once -- the
+ * multi-RHS MULT (Sec. II-B; the links and clover blocks of a site block
+ * read once for all right-hand sides) and a second half whose blocks of one
+ * site block's right-hand sides run together -- with each right-hand side's
+ * own scalars, dot products and exit test; a converged right-hand side is
+ * skipped.  Each x_r equals what qcd_solve returns for b_r, bit for bit.
+ * b, x: device memory, nrhs canonical full-lattice complex128 vectors back
+ * to back ([nrhs][V][4][3]); caller-owned.  infos: NULL or nrhs entries.
+ * opts: precision_levels 2, even_odd 1, use_x0 0, outer_df64 0 or 1,
+ * eo_hermitian 0 (anything else: QCD_EINVAL); 1 <= nrhs <= 16.  The
+ * context keeps a workspace of about 16 FP64 and 7 FP32 half vectors per
+ * right-hand side until it is destroyed.  Returns QCD_OK when every
+ * right-hand side converged, else the first failing status (each entry of
+ * infos has its own). */
+int qcd_solve_multi(qcd_ctx *ctx, const void *b, void *x, int nrhs, double tol, const qcd_solve_opts *opts,
+                    qcd_solve_info *infos);
+
 /* Batched solves: n independent problems, problem i solving D_i x_i = b_i on
  * the lattice, gauge field and clover term of context ctxs[i] (distinct
  * contexts on one device; their lattices may differ), each to

@@ -569,6 +569,40 @@ extern "C" int qcd_solve(qcd_ctx *c, const void *b, void *x, double tol, const q
     return rc;
 }
 
+// ---------------------------------------------------------------- lockstep multi-RHS
+extern "C" int qcd_solve_multi(qcd_ctx *c, const void *b, void *x, int nrhs, double tol, const qcd_solve_opts *opts,
+                               qcd_solve_info *infos)
+{
+    if (!c || !b || !x) {
+        set_error_message("null argument");
+        return QCD_EINVAL;
+    }
+    if (nrhs < 1 || nrhs > 16) {
+        set_error_message("qcd_solve_multi: nrhs = %d outside 1..16", nrhs);
+        return QCD_EINVAL;
+    }
+    qcd_solve_opts o;
+    qcd_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision_levels != 2 || !o.even_odd || o.use_x0 || !(tol > 0.0) || o.max_outer < 1 ||
+        o.max_inner[0] < 1 || !(o.inner_tol[0] > 0.0) || o.max_restarts < 0 || o.outer_df64 < 0 ||
+        o.outer_df64 > 1 || o.eo_hermitian != 0) {
+        set_error_message("qcd_solve_multi: two levels, even-odd D^_ee, x = 0 start, outer_df64 0 or 1");
+        return QCD_EINVAL;
+    }
+    if (!c->have_clover) {
+        set_error_message("qcd_solve_multi needs qcd_gauge_load and qcd_clover_build first");
+        return QCD_ESTATE;
+    }
+    if (!is_device_ptr(b) || !is_device_ptr(x)) {
+        set_error_message("qcd_solve_multi: b and x must be device memory");
+        return QCD_EINVAL;
+    }
+    c->x_host = nullptr;
+    QCD_CUDA_CHECK(cudaMemsetAsync(c->counters, 0, 64 * sizeof(unsigned), c->stream));
+    return solve_multi(c, b, x, nrhs, tol, o, infos);
+}
+
 // ---------------------------------------------------------------- batched
 static long long g_wait_limit = 10000000LL;  // ~1 s of bounded spinning per device wait
 static int g_use_graphs = 1;

@@ -72,6 +72,10 @@ __global__ void k_state_init(SolverState *st, double tol2, double tol2_rel, int 
     *st = s;
 }
 
+// a right-hand side that takes no part in a lockstep inner solve: its
+// kernels return at once
+__global__ void k_state_mark_done(SolverState *st) { st->done = 1; }
+
 // dst->tol2 = factor * src->norm2[slot]
 __global__ void k_set_tol2(SolverState *dst, const SolverState *src, int slot, double factor)
 {
@@ -91,6 +95,14 @@ int state_init(qcd_ctx *c, SolverState *st, double tol2, double tol2_rel, int ma
 {
     c->launches += 1;
     k_state_init<<<1, 1, 0, c->stream>>>(st, tol2, tol2_rel, maxit, bd_eps, unit);
+    QCD_CUDA_CHECK(cudaGetLastError());
+    return QCD_OK;
+}
+
+int state_mark_done(qcd_ctx *c, SolverState *st)
+{
+    c->launches += 1;
+    k_state_mark_done<<<1, 1, 0, c->stream>>>(st);
     QCD_CUDA_CHECK(cudaGetLastError());
     return QCD_OK;
 }

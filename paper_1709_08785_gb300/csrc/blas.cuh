@@ -9,6 +9,7 @@ namespace qcd {
 size_t hvec_elems(const Geom &g, int prec);
 int state_init(qcd_ctx *c, SolverState *st, double tol2, double tol2_rel, int maxit, double bd_eps, int unit);
 int set_tol2(qcd_ctx *c, SolverState *dst, const SolverState *src, int slot, double factor);
+int state_mark_done(qcd_ctx *c, SolverState *st);
 int blas_update_s(qcd_ctx *c, int prec, int n, HVec r, HVec q, SolverState *st);
 int blas_update_x(qcd_ctx *c, int prec, int n, HVec x, HVec p, HVec r, HVec t, HVec rt, SolverState *st);
 int blas_update_p(qcd_ctx *c, int prec, int n, HVec p, HVec r, HVec q, SolverState *st, int fin);

@@ -174,6 +174,10 @@ struct qcd_ctx {
     // batched solves led by this context: problem descriptors, barrier words
     void *batch_buf = nullptr;
     size_t batch_bytes = 0;
+
+    // lockstep multi-RHS solves: per-RHS vectors, states and partials
+    void *multi_buf = nullptr;
+    size_t multi_bytes = 0;
 };
 
 namespace qcd {
@@ -220,6 +224,14 @@ struct StencilCall {
     const int *done = nullptr;
     int force_variant = -1;  // >= 0: bypass the tuned configuration (autotuner)
     int force_bx = 128;
+    // Lockstep multi-RHS solves: each right-hand side has its own solver
+    // state (done flag every done_stride ints, reduction state red_args.st + r)
+    // and, for a second half with fused dots, its own reduction: partials
+    // red_args.partials + r red_pstride, counter red_args.counter + r.  With
+    // rhs_grid the right-hand sides run as the fastest grid dimension.
+    int done_stride = 0;
+    size_t red_pstride = 0;
+    bool rhs_grid = false;
 };
 int launch_stencil(qcd_ctx *c, const StencilCall &s);
 unsigned tune_key(const StencilCall &s);
@@ -236,6 +248,8 @@ int clover_apply_half(qcd_ctx *c, int prec, int parity, int inverse, HVec in, HV
 
 // solver.cu
 int solve(qcd_ctx *c, const void *b_dev, void *x_dev, double tol, const qcd_solve_opts &o, qcd_solve_info *info);
+int solve_multi(qcd_ctx *c, const void *b_dev, void *x_dev, int nrhs, double tol, const qcd_solve_opts &o,
+                qcd_solve_info *info);
 
 // batched.cu
 int batched_solve(qcd_ctx **ctxs, int n, const void *const *b, void *const *x, const double *tol,

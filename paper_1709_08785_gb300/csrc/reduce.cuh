@@ -139,8 +139,12 @@ __device__ inline void finalize(int op, SolverState *st)
 // FP32 and FP16 levels, whose sums feed FP32 recurrences: GB300's FP64 rate
 // is 1/64 of its FP32 rate, and per-thread FP64 adds slowed those kernels
 // in proportion to their size); warp sums and everything after are FP64.
+// bidx / nblk: the block's index among the nblk blocks of this reduction
+// (blockIdx.x / gridDim.x, or another grid dimension when several
+// reductions share one launch); the block with index nblk - 1 is dispatched
+// after every other block of its reduction.
 template <int N, class A>
-__device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
+__device__ __forceinline__ void grid_reduce_ex(A v[N], const RedArgs &ra, int bidx, int nblk)
 {
     __shared__ double sh[32][4];
     __shared__ int last;
@@ -154,7 +158,7 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < N; ++k) sh[wid][k] = (double)v[k];
-    if (blockIdx.x != gridDim.x - 1) {
+    if (bidx != nblk - 1) {
         // Every block but the last: warps 1.. post their sums and leave at
         // once (bar.arrive does not wait; their output stores proceed), warp
         // 0 waits for them (bar.sync on the same named barrier), adds the
@@ -175,7 +179,7 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < N; ++k) ra.partials[(size_t)blockIdx.x * 4 + k] = bsum[k];
+            for (int k = 0; k < N; ++k) ra.partials[(size_t)bidx * 4 + k] = bsum[k];
             // the partial ordered before the count; no reply awaited
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ra.counter) : "memory");
         }
@@ -193,10 +197,10 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < N; ++k) ra.partials[(size_t)blockIdx.x * 4 + k] = bsum[k];
+            for (int k = 0; k < N; ++k) ra.partials[(size_t)bidx * 4 + k] = bsum[k];
             // the highest-indexed block is dispatched last: it waits
             // (bounded) until every other block has counted
-            const unsigned want = gridDim.x - 1;
+            const unsigned want = (unsigned)nblk - 1;
             long long n = 0;
             unsigned got;
             for (;;) {
@@ -222,7 +226,7 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
     for (int k = 0; k < N; ++k) s[k] = 0.0;
     // eight independent loads in flight per thread, the last batch
     // predicated: the partials arrive in ceil(G / 8 nthr) L2 round trips
-    const int G = (int)gridDim.x;
+    const int G = nblk;
     for (int b0 = tid; b0 < G; b0 += 8 * nthr) {
         double t[8][N];
 #pragma unroll
@@ -257,6 +261,12 @@ __device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
         // state and the counter to the next kernel in stream order
         *ra.counter = 0u;
     }
+}
+
+template <int N, class A>
+__device__ __forceinline__ void grid_reduce(A v[N], const RedArgs &ra)
+{
+    grid_reduce_ex<N, A>(v, ra, (int)blockIdx.x, (int)gridDim.x);
 }
 
 }  // namespace qcd

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "blas.cuh"
 
@@ -607,6 +608,377 @@ int solve_full(Solver &S, const void *b, void *x, double tol)
     return status;
 }
 
+// ---------------------------------------------------------------- lockstep multi-RHS solves
+// n systems D x_r = b_r on one gauge field, solved together: every FP32
+// iteration (Alg. 2) applies D^ to all right-hand sides at once -- the
+// multi-RHS MULT, which stages each site block's links and clover once for
+// all of them, and a second half whose blocks of one site block's
+// right-hand sides are dispatched together -- with each right-hand side's
+// own scalars, dot products and exit test; Alg. 1, the FP64 source,
+// reconstruction and true-residual check run right-hand side by right-hand
+// side.  A right-hand side that has converged is skipped.  Each right-hand
+// side repeats qcd_solve's operations in qcd_solve's order (the multi-RHS
+// MULT equals the single-RHS one to the bit, the second half and the BLAS
+// passes are the single-RHS launch shapes), so its solution equals
+// qcd_solve's to the bit.
+struct Multi {
+    qcd_ctx *c = nullptr;
+    qcd_solve_opts o;
+    int n = 0;
+    int P0 = QCD_F64, PX = QCD_F64;
+    std::vector<Solver> S;        // per right-hand side: outer level, b_e, b_o, b^_e, x_o, residual vectors
+    std::vector<HVec> xe0;        // x_e in the outer operator's precision (restarts)
+    HVec X, R, RT, P, Q, T, TMP;  // FP32 level: n vectors each, rhs_stride apart
+    size_t stride32 = 0;          // in 16-byte elements
+    SolverState *st = nullptr;    // [3][n]: inner (contiguous: the lockstep kernels index it), outer, aux
+    double *partials = nullptr;   // [n][pstride]
+    size_t pstride = 0;           // doubles
+    unsigned *counters = nullptr; // [n]
+    std::vector<SolverState> h;   // host copies of the 3 n states
+    SolverState *in(int r) { return st + r; }
+    SolverState *out(int r) { return st + n + r; }
+    SolverState *aux(int r) { return st + 2 * n + r; }
+};
+
+HVec rhs_at(const HVec &v, int r, size_t stride)
+{
+    HVec o = v;
+    o.p = (char *)v.p + (size_t)r * stride * 16;
+    return o;
+}
+
+int read_multi(Multi &M)
+{
+    const size_t bytes = 3 * (size_t)M.n * sizeof(SolverState);
+    QCD_CUDA_CHECK(cudaMemcpyAsync(M.h.data(), M.st, bytes, cudaMemcpyDeviceToHost, M.c->stream));
+    QCD_CUDA_CHECK(cudaStreamSynchronize(M.c->stream));
+    return QCD_OK;
+}
+
+// one device allocation for every per-RHS vector, state and partial
+int multi_workspace(Multi &M)
+{
+    qcd_ctx *c = M.c;
+    const int n = M.n;
+    const size_t h64 = hvec_bytes(c->g, QCD_F64), h32 = hvec_bytes(c->g, QCD_F32);  // DF64 is FP64-sized
+    const size_t G = nblocks(c->g.Vh, 32);  // partials of the smallest block the tuner uses
+    M.pstride = G * 4;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b64 = up(16 * (size_t)n * h64), b32 = up(7 * (size_t)n * h32);
+    const size_t bst = up(3 * (size_t)n * sizeof(SolverState)), bpart = up((size_t)n * M.pstride * sizeof(double));
+    const size_t need = b64 + b32 + bst + bpart + up(n * sizeof(unsigned));
+    if (c->multi_bytes < need) {
+        if (c->multi_buf) {
+            QCD_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+            cudaFree(c->multi_buf);
+            for (void *&q : c->pool)
+                if (q == c->multi_buf) q = nullptr;
+            c->multi_buf = nullptr;
+            c->multi_bytes = 0;
+        }
+        TRY(dev_alloc(c, &c->multi_buf, need));
+        c->multi_bytes = need;
+    }
+    char *base = (char *)c->multi_buf;
+    auto v64 = [&](int k, int r, int prec) {
+        HVec v;
+        v.p = base + ((size_t)k * n + r) * h64;
+        v.prec = prec;
+        return v;
+    };
+    M.S.assign(n, Solver{});
+    M.xe0.assign(n, HVec{});
+    for (int r = 0; r < n; ++r) {
+        Solver &S = M.S[r];
+        S.c = c;
+        S.o = M.o;
+        std::memset(&S.info, 0, sizeof(S.info));
+        S.be = v64(0, r, QCD_F64);
+        S.bo = v64(1, r, QCD_F64);
+        S.bhat = v64(2, r, QCD_F64);
+        S.xo = v64(3, r, QCD_F64);
+        S.re = v64(4, r, QCD_F64);
+        S.ro = v64(5, r, QCD_F64);
+        Level &O = S.lv[0];
+        O.prec = M.P0;
+        O.form = 0;
+        O.x = v64(6, r, QCD_F64);  // the solution x_e is FP64 in both outer modes
+        HVec *lv[7] = {&O.r, &O.rt, &O.p, &O.q, &O.t, &O.v, &O.tmp};
+        for (int k = 0; k < 7; ++k) *lv[k] = v64(7 + k, r, M.P0);
+        S.bhat0 = M.PX != M.P0 ? v64(14, r, M.P0) : S.bhat;
+        M.xe0[r] = M.PX != M.P0 ? v64(15, r, M.P0) : O.x;
+    }
+    char *p32 = base + b64;
+    M.stride32 = hvec_elems(c->g, QCD_F32);
+    HVec *a32[7] = {&M.X, &M.R, &M.RT, &M.P, &M.Q, &M.T, &M.TMP};
+    for (int k = 0; k < 7; ++k) {
+        a32[k]->p = p32 + (size_t)k * n * h32;
+        a32[k]->norm = nullptr;
+        a32[k]->prec = QCD_F32;
+    }
+    M.st = (SolverState *)(base + b64 + b32);
+    M.partials = (double *)(base + b64 + b32 + bst);
+    M.counters = (unsigned *)(base + b64 + b32 + bst + bpart);
+    for (int r = 0; r < n; ++r) {
+        M.S[r].lv[0].st = M.out(r);
+        M.S[r].aux = M.aux(r);
+    }
+    M.h.assign(3 * (size_t)n, SolverState{});
+    QCD_CUDA_CHECK(cudaMemsetAsync(M.counters, 0, n * sizeof(unsigned), c->stream));
+    return QCD_OK;
+}
+
+// one Alg. 2 iteration of every right-hand side of the FP32 level
+int bicg_iteration_multi(Multi &M)
+{
+    qcd_ctx *c = M.c;
+    const int ns = c->g.Vh_pad, n = M.n;
+    const int dstride = (int)(sizeof(SolverState) / sizeof(int));
+    auto half = [&](HVec in, HVec out, int red, HVec aux, int fin) -> int {
+        StencilCall s1;
+        s1.prec = QCD_F32;
+        s1.mode = M_MULT;
+        s1.out_par = 1;
+        s1.out = M.TMP;
+        s1.in = in;
+        s1.nrhs = n;
+        s1.rhs_stride = M.stride32;
+        s1.done = &M.in(0)->done;
+        s1.done_stride = dstride;
+        TRY(launch_stencil(c, s1));
+        StencilCall s2;
+        s2.prec = QCD_F32;
+        s2.mode = M_DHAT;
+        s2.out_par = 0;
+        s2.out = out;
+        s2.in = M.TMP;
+        s2.y = in;
+        s2.a = 1.0;
+        s2.cc = -c->kappa * c->kappa;
+        s2.red = red;
+        s2.aux = aux;
+        s2.red_args = RedArgs{M.partials, M.counters, M.in(0), fin};
+        s2.nrhs = n;
+        s2.rhs_stride = M.stride32;
+        s2.done = &M.in(0)->done;
+        s2.done_stride = dstride;
+        s2.red_pstride = M.pstride;
+        s2.rhs_grid = true;
+        return launch_stencil(c, s2);
+    };
+    auto at = [&](const HVec &v, int r) { return rhs_at(v, r, M.stride32); };
+    TRY(half(M.P, M.Q, R_DOT_AUX, M.RT, FIN_ALPHA));  // q = D^ p, alpha
+    for (int r = 0; r < n; ++r) TRY(blas_update_s(c, QCD_F32, ns, at(M.R, r), at(M.Q, r), M.in(r)));  // s = r - alpha q
+    TRY(half(M.R, M.T, R_OMEGA, M.R, FIN_OMEGA));  // t = D^ s, omega
+    for (int r = 0; r < n; ++r)
+        TRY(blas_update_x(c, QCD_F32, ns, at(M.X, r), at(M.P, r), at(M.R, r), at(M.T, r), at(M.RT, r), M.in(r)));
+    for (int r = 0; r < n; ++r) TRY(blas_update_p(c, QCD_F32, ns, at(M.P, r), at(M.R, r), at(M.Q, r), M.in(r), FIN_NONE));
+    return QCD_OK;
+}
+
+// v_r = M src_r for the right-hand sides in `act`: Alg. 2 in FP32 on the
+// unit-norm src_r / |src_r|, all of them in lockstep, lifted back
+int precondition_multi(Multi &M, const std::vector<char> &act, const std::vector<HVec> &src,
+                       const std::vector<const double *> &src_norm2, const std::vector<HVec> &v)
+{
+    qcd_ctx *c = M.c;
+    const int ns = c->g.Vh_pad, n = M.n;
+    const double tol = M.o.inner_tol[0];
+    auto at = [&](const HVec &x, int r) { return rhs_at(x, r, M.stride32); };
+    for (int r = 0; r < n; ++r) {
+        TRY(state_init(c, M.in(r), tol * tol, 0.0, M.o.max_inner[0], BD_EPS_LOW, 1));
+        if (act[r])
+            TRY(blas_inner_init(c, M.P0, QCD_F32, ns, src[r], src_norm2[r], at(M.R, r), at(M.RT, r), at(M.P, r),
+                                at(M.X, r), &M.out(r)->done));
+        else TRY(state_mark_done(c, M.in(r)));
+    }
+    int queued = 0, chunk = 3, maxit = M.o.max_inner[0];
+    std::vector<double> rr0(n, -1.0);
+    for (;;) {
+        for (int k = 0; k < chunk; ++k) TRY(bicg_iteration_multi(M));
+        queued += chunk;
+        TRY(read_multi(M));
+        int pred = 1;
+        bool all = true;
+        for (int r = 0; r < n; ++r) {
+            const SolverState &h = M.h[r];
+            if (rr0[r] < 0.0) rr0[r] = h.rr > 0 ? h.rr : 1.0;
+            if (h.done) continue;
+            all = false;
+            // the remaining iterations predicted from this right-hand side's contraction so far
+            int pr = 8;
+            if (h.iter > 0 && h.rr > 0.0 && h.rr < rr0[r] && h.tol2 > 0.0) {
+                const double rate = std::log(h.rr / rr0[r]) / h.iter;
+                pr = (int)std::ceil(std::log(h.tol2 / h.rr) / rate);
+            }
+            if (pr < 2) pr = 2;
+            if (pr > maxit - h.iter + 1) pr = maxit - h.iter + 1;
+            if (pr > pred) pred = pr;
+        }
+        if (all) break;
+        if (queued > maxit + 8) {  // cannot happen: FIN_X caps every right-hand side at maxit
+            set_error_message("iteration queue overran the cap");
+            return QCD_ETIMEOUT;
+        }
+        chunk = pred > 64 ? 64 : pred < 1 ? 1 : pred;
+    }
+    for (int r = 0; r < n; ++r) {
+        if (!act[r]) continue;
+        const SolverState &h = M.h[r];
+        M.S[r].info.inner_iters[0] += h.iter;
+        M.S[r].info.dhat_applies[QCD_F32] += 2L * h.iter - h.exit_half;
+        TRY(blas_finish_half(c, QCD_F32, ns, at(M.X, r), at(M.P, r), M.in(r)));
+        TRY(blas_lift(c, QCD_F32, M.P0, ns, at(M.X, r), v[r], src_norm2[r], &M.out(r)->done));
+    }
+    return QCD_OK;
+}
+
+// Alg. 1 for the right-hand sides in `act` until each has converged
+int flexible_multi(Multi &M, std::vector<char> act)
+{
+    qcd_ctx *c = M.c;
+    const int ns = c->g.Vh_pad, n = M.n;
+    std::vector<HVec> src(n), v(n);
+    std::vector<const double *> nrm(n);
+    auto refresh = [&]() -> int {  // drop the right-hand sides whose outer level is done
+        TRY(read_multi(M));
+        int left = 0;
+        for (int r = 0; r < n; ++r) {
+            if (act[r] && M.h[n + r].done) act[r] = 0;
+            left += act[r];
+        }
+        return left;
+    };
+    int left = refresh();
+    if (left < 0) return left;
+    while (left > 0) {
+        for (int r = 0; r < n; ++r) {
+            Level &O = M.S[r].lv[0];
+            src[r] = O.p;
+            nrm[r] = &O.st->norm2[1];
+            v[r] = O.v;
+        }
+        TRY(precondition_multi(M, act, src, nrm, v));  // v = M p
+        for (int r = 0; r < n; ++r) {
+            if (!act[r]) continue;
+            Level &O = M.S[r].lv[0];
+            TRY(dhat(c, O.prec, O.v, O.q, O.tmp, R_DOT_AUX, O.rt, O.st, FIN_ALPHA, &O.st->done, 0));  // q = D^ v, alpha
+            TRY(blas_flex1(c, O.prec, ns, O.x, O.v, O.r, O.q, O.st));                                    // x, r, |r|
+            M.S[r].info.dhat_applies[QCD_F64] += 1;
+        }
+        if ((left = refresh()) <= 0) break;
+        for (int r = 0; r < n; ++r) {
+            Level &O = M.S[r].lv[0];
+            src[r] = O.r;
+            nrm[r] = &O.st->rr;
+        }
+        TRY(precondition_multi(M, act, src, nrm, v));  // v = M r
+        for (int r = 0; r < n; ++r) {
+            if (!act[r]) continue;
+            Level &O = M.S[r].lv[0];
+            TRY(dhat(c, O.prec, O.v, O.t, O.tmp, R_OMEGA, O.r, O.st, FIN_OMEGA, &O.st->done, 0));  // t = D^ v, omega
+            TRY(blas_flex2(c, O.prec, ns, O.x, O.v, O.r, O.t, O.rt, O.st));                         // x, r, beta
+            TRY(blas_update_p(c, O.prec, ns, O.p, O.r, O.q, O.st, FIN_SETN + 1));                   // p, |p|
+            M.S[r].info.dhat_applies[QCD_F64] += 1;
+        }
+        left = refresh();
+    }
+    return left < 0 ? left : QCD_OK;
+}
+
+// the n solves: b, x hold n full-lattice complex128 vectors back to back
+int solve_multi_eo(Multi &M, const void *b, void *x, double tol, std::vector<int> &status)
+{
+    qcd_ctx *c = M.c;
+    const int ns = c->g.Vh_pad, n = M.n;
+    const size_t vbytes = (size_t)c->g.V * 12 * 16;
+    const int maxit = M.o.max_outer;
+    for (int r = 0; r < n; ++r) {
+        Solver &S = M.S[r];
+        Level &O = S.lv[0];
+        const void *br = (const char *)b + r * vbytes;
+        TRY(canon_to_half(c, QCD_F64, 0, br, 0, S.be, 1, 0));
+        TRY(canon_to_half(c, QCD_F64, 0, br, 1, S.bo, 1, 0));
+        TRY(state_init(c, S.aux, 0.0, 0.0, 0, 0.0, 0));
+        TRY(blas_norm2(c, QCD_F64, ns, S.be, S.aux, FIN_SETN + 0));
+        TRY(blas_norm2(c, QCD_F64, ns, S.bo, S.aux, FIN_ADDN + 0));
+        // b^_e = F_ee^-1 (b_e + kappa H_eo F_oo^-1 b_o)   (Eq. 6), in FP64
+        TRY(clover_apply_half(c, QCD_F64, 1, 1, S.bo, S.re, 1, 0));
+        StencilCall s;
+        s.prec = QCD_F64;
+        s.mode = M_SRC;
+        s.out_par = 0;
+        s.out = S.bhat;
+        s.in = S.re;
+        s.y = S.be;
+        s.a = 1.0;
+        s.cc = c->kappa;
+        TRY(launch_stencil(c, s));
+        if (M.PX != M.P0) TRY(convert_half(c, S.bhat, S.bhat0));
+        TRY(state_init(c, O.st, 0.0, 0.0, maxit, BD_EPS_F64, 0));
+        TRY(set_tol2(c, O.st, S.aux, 0, 0.25 * tol * tol));
+        TRY(blas_init(c, M.P0, ns, S.bhat0, O.r, O.rt, O.p, O.x, 1, O.st, FIN_INIT));
+    }
+    std::vector<char> act(n, 1);
+    status.assign(n, QCD_OK);
+    for (int restart = 0;; ++restart) {
+        TRY(flexible_multi(M, act));
+        // x_o = F_oo^-1 (b_o + kappa H_oe x_e) with the odd rows of b - D x
+        // (Eq. 7), the even rows, x out: FP64, per right-hand side
+        for (int r = 0; r < n; ++r) {
+            if (!act[r]) continue;
+            Solver &S = M.S[r];
+            StencilCall s;
+            s.prec = QCD_F64;
+            s.mode = M_RECON;
+            s.out_par = 1;
+            s.out = S.xo;
+            s.in = S.lv[0].x;
+            s.y = S.bo;
+            s.a = 1.0;
+            s.cc = c->kappa;
+            s.red = R_NORM;
+            s.red_args = RedArgs{c->partials, c->counters, S.aux, FIN_SETN + 2};
+            TRY(launch_stencil(c, s));
+            TRY(emit_x(c, S.lv[0].x, S.xo, (char *)x + r * vbytes));
+            TRY(residual_even(S, S.lv[0].x, S.xo));
+        }
+        TRY(read_multi(M));
+        std::vector<char> again(n, 0);
+        int nagain = 0;
+        for (int r = 0; r < n; ++r) {
+            if (!act[r]) continue;
+            Solver &S = M.S[r];
+            const SolverState &ho = M.h[n + r], &ha = M.h[2 * n + r];
+            S.info.outer_iters = ho.iter;
+            S.info.true_resid = resid_ratio(ha);
+            int st = ho.status;
+            if (!std::isfinite(S.info.true_resid)) st = QCD_ENONFINITE;
+            else if (S.info.true_resid <= tol) st = QCD_OK;
+            else if (st != QCD_ENONFINITE && restart < M.o.max_restarts && ho.iter < maxit) {
+                again[r] = 1;
+                ++nagain;
+            } else if (st == QCD_OK) st = QCD_ENOTCONV;
+            status[r] = st;
+        }
+        if (!nagain) break;
+        // restart from the recomputed residual r = b^ - D^ x_e
+        for (int r = 0; r < n; ++r) {
+            if (!again[r]) continue;
+            Solver &S = M.S[r];
+            Level &O = S.lv[0];
+            S.info.restarts += 1;
+            TRY(state_init(c, O.st, 0.0, 0.0, maxit, BD_EPS_F64, 0));
+            TRY(set_tol2(c, O.st, S.aux, 0, 0.25 * tol * tol));
+            if (M.PX != M.P0) TRY(convert_half(c, O.x, M.xe0[r]));
+            TRY(residual_eo(S, M.xe0[r], O.r, O.st, FIN_NONE));
+            TRY(blas_init(c, M.P0, ns, O.r, O.r, O.rt, O.p, O.x, 0, O.st, FIN_RESTART));
+        }
+        act = again;
+    }
+    return QCD_OK;
+}
+
 }  // namespace
 
 int solve(qcd_ctx *c, const void *b_dev, void *x_dev, double tol, const qcd_solve_opts &o, qcd_solve_info *info)
@@ -630,6 +1002,39 @@ int solve(qcd_ctx *c, const void *b_dev, void *x_dev, double tol, const qcd_solv
     S.info.status = rc;
     if (info) *info = S.info;
     return rc;
+}
+
+int solve_multi(qcd_ctx *c, const void *b_dev, void *x_dev, int nrhs, double tol, const qcd_solve_opts &o,
+                qcd_solve_info *info)
+{
+    Multi M;
+    M.c = c;
+    M.o = o;
+    M.n = nrhs;
+    M.P0 = o.outer_df64 ? QCD_DF64 : QCD_F64;
+    M.PX = QCD_F64;
+    cudaEvent_t e0, e1;
+    QCD_CUDA_CHECK(cudaEventCreate(&e0));
+    QCD_CUDA_CHECK(cudaEventCreate(&e1));
+    QCD_CUDA_CHECK(cudaEventRecord(e0, c->stream));
+    std::vector<int> status;
+    int rc = multi_workspace(M);
+    if (rc == QCD_OK) rc = solve_multi_eo(M, b_dev, x_dev, tol, status);
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int worst = rc;
+    for (int r = 0; r < nrhs && r < (int)M.S.size(); ++r) {
+        qcd_solve_info &in = M.S[r].info;
+        in.seconds = ms * 1e-3;
+        in.status = rc != QCD_OK ? rc : r < (int)status.size() ? status[r] : QCD_ESTATE;
+        if (worst == QCD_OK && in.status != QCD_OK) worst = in.status;
+        if (info) info[r] = in;
+    }
+    return worst;
 }
 
 }  // namespace qcd

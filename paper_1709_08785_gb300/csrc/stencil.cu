@@ -21,6 +21,7 @@ namespace qcd {
 // per-precision instantiations (stencil_<prec>.cu) and the multi-RHS kernel
 int dispatch_f64(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int v);
 int dispatch_f32(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int v);
+int dispatch_f32_rg(const StencilCall &sc, const StencilArgs &A, int bx, cudaStream_t s, int v);
 int dispatch_f16(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int v);
 int dispatch_df64(const StencilCall &sc, const StencilArgs &A, dim3 grid, dim3 block, cudaStream_t s, int v);
 int launch_mrhs(const StencilCall &sc, const StencilArgs &A, int nrhs, cudaStream_t s, int variant, int tile,
@@ -90,10 +91,42 @@ int launch_stencil(qcd_ctx *c, const StencilCall &sc)
     A.nrhs = sc.nrhs < 1 ? 1 : sc.nrhs;
     A.red = sc.red_args;
     A.done = sc.done;
+    A.done_stride = sc.done_stride;
+    A.red_pstride = sc.red_pstride;
+    A.skip = nullptr;
     const int nrhs = sc.nrhs < 1 ? 1 : sc.nrhs;
     if (nrhs > 16) {
         set_error_message("nrhs > 16 per launch");
         return QCD_EINVAL;
+    }
+    if (sc.rhs_grid) {
+        // a lockstep second half: the single-RHS entry's register budget and
+        // sites per block, so that every right-hand side repeats the
+        // single-RHS launch's arithmetic and reduction order
+        if (p != QCD_F32 || sc.mode != M_DHAT || (sc.red != R_DOT_AUX && sc.red != R_OMEGA) ||
+            sc.done_stride < 1 || !sc.red_pstride) {
+            set_error_message("rhs_grid: FP32 D^ second halves with per-RHS states and partials only");
+            return QCD_EINVAL;
+        }
+        StencilCall one = sc;
+        one.nrhs = 1;
+        one.rhs_grid = false;
+        int v = 0, b = 128;
+        auto it = c->tune.find(tune_key(one));
+        if (it != c->tune.end()) {
+            v = it->second.variant;
+            b = it->second.bx;
+        }
+        if (v != 1) v = 0;  // the rolled and pipelined hops have no lockstep form: the plain kernel
+        if ((size_t)nblocks(c->g.Vh, b) * 4 > sc.red_pstride) {
+            set_error_message("rhs_grid: %u partials per right-hand side do not fit", nblocks(c->g.Vh, b));
+            return QCD_EINVAL;
+        }
+        const int rc = dispatch_f32_rg(sc, A, b, c->stream, v);
+        if (rc != QCD_OK) return rc;
+        c->launches += 1;
+        QCD_CUDA_CHECK(cudaGetLastError());
+        return QCD_OK;
     }
     int bx = 128, variant = 0;  // bx: sites per block, or for the multi-RHS kernel the RHS tile
     if (nrhs > 1) bx = is_mrhs(sc) ? nrhs : nrhs <= 4 ? 64 : 32;

@@ -658,6 +658,8 @@ struct StencilArgs {
     const int *done;
     int *skip;  // profiling: set to 1 when the launch returns early
     int nrhs;   // right-hand sides of the launch (multi-RHS: blockIdx.y selects a tile of them)
+    int done_stride;      // lockstep solves: right-hand side r's done flag is done[r done_stride]
+    size_t red_pstride;   // and its reduction's partials start red.partials + r red_pstride
 };
 
 // a host-supplied scalar in the kernel's arithmetic type (float: the

@@ -220,6 +220,73 @@ __global__ void __launch_bounds__(256) stencil_kernel_pipe(StencilArgs A)
     if constexpr (P == QCD_F32 || P == QCD_F16) stencil_body_pipe<P, MODE, RED, DAG>(A);
 }
 
+// Second halves with fused dot products for a lockstep multi-RHS solve: the
+// right-hand sides run as the fastest grid dimension (blockIdx.x = r,
+// blockIdx.y = site block), so the blocks of one site block's right-hand
+// sides are dispatched together and read its links and clover from HBM once
+// (from L2 for the others); each right-hand side keeps its own reduction
+// (partials, counter, solver state) and its own done flag, and equals the
+// single-RHS kernel's result at the same sites per block to the bit.
+template <int P, int MODE, int RED>
+__device__ __forceinline__ void stencil_body_rg(const StencilArgs &A)
+{
+    pdl_enter();
+    const int r = blockIdx.x;
+    if (A.done && A.done[(size_t)r * A.done_stride]) return;  // uniform over the blocks of r
+    using RA = typename std::conditional<P == QCD_F32 || P == QCD_F16, float, double>::type;
+    RA red[4] = {RA(0), RA(0), RA(0), RA(0)};
+    const int cb = blockIdx.y * blockDim.x + threadIdx.x;
+    using T = typename Prec<P>::T;
+    Spinor<T> acc;
+    bool pending = false;
+    if (cb < A.g.Vh) {
+        const SpinorPtr in = rhs_ptr(A.in, r, A.rhs_stride, A.norm_stride);
+        pending = stencil_site<P, MODE, RED, false>(
+            A, cb, r, red, acc, [&](Spinor<T> &a) { hopping_any<P, false>(A.g, A.U, in, A.out_par, cb, a); },
+            [&](Spinor<T> &x) { clover_any<P>(A.C, A.out_par, cb, x); });
+    }
+    RedArgs ra = A.red;
+    ra.partials += (size_t)r * A.red_pstride;
+    ra.counter += r;
+    ra.st += r;
+    grid_reduce_ex<RED == R_OMEGA ? 3 : RED == R_DOT_AUX ? 2 : 1>(red, ra, (int)blockIdx.y, (int)gridDim.y);
+    if (pending) Prec<P>::store(rhs_ptr(A.out, r, A.rhs_stride, A.norm_stride), cb, acc);
+}
+
+template <int P, int MODE, int RED>
+__global__ void __launch_bounds__(384) stencil_kernel_rg(StencilArgs A)
+{
+    stencil_body_rg<P, MODE, RED>(A);
+}
+
+template <int P, int MODE, int RED>
+__global__ void __maxnreg__(80) stencil_kernel_rg_r80(StencilArgs A)
+{
+    stencil_body_rg<P, MODE, RED>(A);
+}
+
+// the launcher of the lockstep second halves (FP32 D^_ee with <r~|q> or
+// omega): grid (nrhs, site blocks), the single-RHS entry's register budget
+template <int P>
+int dispatch_rg(const StencilCall &sc, const StencilArgs &A, int bx, cudaStream_t s, int variant)
+{
+    if constexpr (P == QCD_F32) {
+        const dim3 grid(A.nrhs, nblocks(A.g.Vh, bx)), block(bx);
+        if (sc.mode == M_DHAT && (sc.red == R_DOT_AUX || sc.red == R_OMEGA)) {
+            if (sc.red == R_DOT_AUX) {
+                if (variant == 1) launch_pdl(stencil_kernel_rg_r80<P, M_DHAT, R_DOT_AUX>, grid, block, 0, s, A);
+                else launch_pdl(stencil_kernel_rg<P, M_DHAT, R_DOT_AUX>, grid, block, 0, s, A);
+            } else {
+                if (variant == 1) launch_pdl(stencil_kernel_rg_r80<P, M_DHAT, R_OMEGA>, grid, block, 0, s, A);
+                else launch_pdl(stencil_kernel_rg<P, M_DHAT, R_OMEGA>, grid, block, 0, s, A);
+            }
+            return QCD_OK;
+        }
+    }
+    set_error_message("the right-hand sides on the grid: FP32 D^ second halves with <r~|q> or omega only");
+    return QCD_EINVAL;
+}
+
 // DF64 (arithmetic-bound, ~165 registers by default): a 128-register cap
 // gives four 128-thread blocks per SM instead of three
 template <int P, int MODE, int RED, bool DAG>

@@ -355,6 +355,14 @@ __device__ __forceinline__ void mrhs_body(const StencilArgs &A)
     const int nthr = blockDim.x * blockDim.y;
     const int nsb = (A.g.Vh + SB - 1) / SB;
     const int r = blockIdx.y * blockDim.y + threadIdx.y;
+    if (A.done) {  // a lockstep solve: nothing to do once every right-hand side of the tile has converged
+        bool all = true;
+        for (int k = 0; k < (int)blockDim.y; ++k) {
+            const int rr = blockIdx.y * blockDim.y + k;
+            if (rr < A.nrhs && !A.done[(size_t)rr * A.done_stride]) all = false;
+        }
+        if (all) return;  // the same decision in every thread: no barrier is left waiting
+    }
     int sb = blockIdx.x, buf = 0;
     if (sb < nsb) mrhs_prefetch<CL>(A, sb * SB, raw_l, raw_c, s_nb, s_tf, tid, nthr);
     cp_wait_all();

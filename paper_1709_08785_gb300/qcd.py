@@ -69,7 +69,7 @@ EXPORTS = [
     "qcd_set_profiling", "qcd_kernel_stats", "qcd_reset_kernel_stats", "qcd_strerror", "qcd_last_error",
     "qcd_volume", "qcd_launch_count", "qcd_mult_benchmark", "qcd_mult_throughput", "qcd_dslash_eo_noalloc",
     "qcd_solve_adjoint", "qcd_force", "qcd_autotune", "qcd_tune_info", "qcd_solve_batched", "qcd_set_wait_limit",
-    "qcd_set_graphs", "qcd_pion_correlator", "qcd_schur_ee",
+    "qcd_set_graphs", "qcd_pion_correlator", "qcd_schur_ee", "qcd_solve_multi",
 ]
 
 _lib = None
@@ -108,6 +108,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.qcd_solve_opts_default.argtypes = [ctypes.POINTER(SolveOpts)]
     lib.qcd_solve_opts_default.restype = None
     lib.qcd_solve.argtypes = [vp, vp, vp, dp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
+    lib.qcd_solve_multi.argtypes = [vp, vp, vp, ip, dp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)]
     lib.qcd_set_profiling.argtypes = [vp, ip]
     lib.qcd_kernel_stats.argtypes = [vp, ip, ctypes.POINTER(KernelStat)]
     lib.qcd_reset_kernel_stats.argtypes = [vp]
@@ -275,6 +276,24 @@ class Context:
         d = info.as_dict()
         d["rc"] = rc
         return d
+
+    def solve_multi(self, b, x, tol: float = 1e-12, opts: SolveOpts | None = None, check: bool = True,
+                    **kw) -> list:
+        """Lockstep solves of the right-hand sides b[r] (device, [nrhs, V, 4, 3]
+        complex128) into x[r]; one info dict per right-hand side."""
+        if opts is None:
+            opts = default_opts(**kw)
+        n = int(b.shape[0])
+        infos = (SolveInfo * n)()
+        rc = self.lib.qcd_solve_multi(self._h, _ptr(b), _ptr(x), n, float(tol), ctypes.byref(opts), infos)
+        if check:
+            _check(rc)
+        out = []
+        for i in range(n):
+            d = infos[i].as_dict()
+            d["rc"] = rc
+            out.append(d)
+        return out
 
     def solve_adjoint(self, g, lam, tol: float = 1e-12, opts: SolveOpts | None = None, check: bool = True,
                       **kw) -> dict:
