@@ -118,7 +118,12 @@ def w_point_sources(args):
     seq, res, outer = 0.0, [], []
     for k in range(12):
         bk = torch.from_numpy(np.ascontiguousarray(P[k])).cuda()
+        # one NVTX range per kind of solve (the first source's), so that a profiler can select it
+        if k == 0:
+            torch.cuda.nvtx.range_push("single_solve")
         t1, info = timed_solve(torch, ctx, bk, X[k], tol, reps=1, precision_levels=2)
+        if k == 0:
+            torch.cuda.nvtx.range_pop()
         seq += t1
         res.append(info["true_resid"])
         outer.append(info["outer_iters"])
@@ -130,13 +135,17 @@ def w_point_sources(args):
     Xm = torch.zeros_like(B)
     ctx.solve_multi(B, Xm, tol=tol, opts=qcd.default_opts(precision_levels=2))
     best, infos = None, None
-    for _ in range(3):
+    for rep in range(3):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if rep == 2:
+            torch.cuda.nvtx.range_push("lockstep_solve")
         e0.record()
         infos = ctx.solve_multi(B, Xm, tol=tol, opts=qcd.default_opts(precision_levels=2))
         e1.record()
         torch.cuda.synchronize()
+        if rep == 2:
+            torch.cuda.nvtx.range_pop()
         t = e0.elapsed_time(e1) * 1e-3
         best = t if best is None else min(best, t)
     out["solves"]["lockstep_s"] = round(best, 4)
