@@ -37,31 +37,31 @@ def sources(dims, kind, n, seed):
     return np.stack([inputs.gaussian_source(dims, seed + k) for k in range(n)])
 
 
-def check_against_single(ctx, U, dims, B, outer_df64):
+def check_against_single(ctx, U, dims, B, outer_df64, tol=1e-12, converge=True, **kw):
     from paper_1709_08785_gb300 import qcd
 
-    opts = qcd.default_opts(precision_levels=2, outer_df64=outer_df64)
+    opts = qcd.default_opts(precision_levels=2, outer_df64=outer_df64, **kw)
     Bd = torch.from_numpy(B).cuda()
     X = torch.zeros_like(Bd)
-    infos = ctx.solve_multi(Bd, X, tol=1e-12, opts=opts)
+    infos = ctx.solve_multi(Bd, X, tol=tol, opts=opts, check=converge)
     torch.cuda.synchronize()
     Xm = X.cpu().numpy()
     F = oracle.clover_field(dims, U, KAPPA, CSW)
     for k in range(B.shape[0]):
         x1 = torch.zeros_like(Bd[k])
-        one = ctx.solve(Bd[k], x1, tol=1e-12, opts=opts)
+        one = ctx.solve(Bd[k], x1, tol=tol, opts=opts, check=converge)
         torch.cuda.synchronize()
         assert np.array_equal(Xm[k], x1.cpu().numpy()), k
         for key in ("outer_iters", "inner_iters", "dhat_applies", "restarts", "status"):
             assert infos[k][key] == one[key], (k, key, infos[k][key], one[key])
         assert infos[k]["true_resid"] == one["true_resid"], k
-        if np.any(B[k]):  # (a zero right-hand side has no relative residual: x = 0 is checked by the caller)
-            assert oracle.true_residual(dims, TBC, U, F, KAPPA, B[k], Xm[k]) <= 1e-12, k
+        if converge and np.any(B[k]):  # (a zero right-hand side has no relative residual: x = 0 is checked by the caller)
+            assert oracle.true_residual(dims, TBC, U, F, KAPPA, B[k], Xm[k]) <= tol, k
     return infos
 
 
 @pytest.mark.parametrize("dims", [(6, 2, 4, 10), (8, 8, 8, 16)])
-@pytest.mark.parametrize("kind,n", [("point", 12), ("gauss", 3)])
+@pytest.mark.parametrize("kind,n", [("point", 12), ("gauss", 3), ("gauss", 1), ("gauss", 16)])
 @pytest.mark.parametrize("outer_df64", [1, 0])
 def test_multi_equals_single_solves(dims, kind, n, outer_df64):
     """Lockstep columns against one qcd_solve per column (untuned launch
@@ -106,6 +106,22 @@ def test_multi_forced_shapes(tmp_path):
     ctx, U = make_ctx(dims, 133, cache)
     assert any(e["threads"] == 4 and e["nrhs"] == 12 for e in ctx.tune_info())
     check_against_single(ctx, U, dims, sources(dims, "point", 12, 0), 1)
+    ctx.close()
+
+
+def test_multi_caps_and_restarts():
+    """The exits that are not convergence, column by column as qcd_solve
+    takes them: the outer iteration cap (QCD_ENOTCONV with no restart left)
+    and a tolerance below what FP64 reaches (5e-16), where a recursive
+    residual below the threshold meets a true residual above it and the
+    solve restarts from the true residual until it runs out of restarts."""
+    dims = (6, 2, 4, 10)
+    ctx, U = make_ctx(dims, 137)
+    B = sources(dims, "gauss", 5, 138)
+    infos = check_against_single(ctx, U, dims, B, 1, converge=False, max_outer=1, max_restarts=0)
+    assert all(i["status"] == -4 and i["restarts"] == 0 for i in infos)  # QCD_ENOTCONV
+    infos = check_against_single(ctx, U, dims, B, 1, tol=5e-16, converge=False, max_restarts=2)
+    assert any(i["restarts"] > 0 for i in infos), [i["restarts"] for i in infos]
     ctx.close()
 
 
