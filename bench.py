@@ -305,8 +305,10 @@ def extra_workloads(torch, qcd, hbm):
     del U
     c.autotune(TUNE_CACHE)
     x = torch.zeros_like(b)
-    t, info = timed_solves(torch, c, b, x, 1e-12, qcd.default_opts(precision_levels=3, inner_tol=[1e-5, 1e-2]), 2)
+    # inner tolerances tuned at this size: FP32 middle level 1e-3, FP16 level 3e-2
+    t, info = timed_solves(torch, c, b, x, 1e-12, qcd.default_opts(precision_levels=3, inner_tol=[1e-3, 3e-2]), 2)
     out["three_level_48x48x48x96"] = solve_summary(t, info)
+    out["three_level_48x48x48x96"]["inner_tol"] = [1e-3, 3e-2]
     r = c.mult_benchmark(qcd.F16, 1, 10)
     out["three_level_48x48x48x96"]["dslash_f16_frac_hbm"] = round(r["gbs"] / hbm, 3)
     c.close()

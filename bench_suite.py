@@ -73,7 +73,10 @@ def w_three_level(args):
     x = torch.zeros_like(b)
     out = {"workload": "48^3x96 clover-Wilson, eps 0.25 seed 4, kappa 0.124, csw 1.6, source seed 40, tol 1e-12",
            "sites": inputs.volume(dims), "input_generation_s": round(gen_s, 1)}
-    for name, kw in (("three_level", dict(precision_levels=3, inner_tol=[1e-5, 1e-2])),
+    # three levels with the inner tolerances tuned at this size (FP32 middle
+    # level 1e-3, FP16 level 3e-2) and with the untuned proposal (1e-5, 1e-2)
+    for name, kw in (("three_level", dict(precision_levels=3, inner_tol=[1e-3, 3e-2])),
+                     ("three_level_untuned_tols", dict(precision_levels=3, inner_tol=[1e-5, 1e-2])),
                      ("two_level", dict(precision_levels=2)),
                      ("fp64_only", dict(precision_levels=1, max_outer=5000))):
         t, info = timed_solve(torch, ctx, b, x, tol, reps=1 if name == "fp64_only" else 2, **kw)

@@ -234,7 +234,9 @@ int qcd_solve(qcd_ctx *ctx, const void *b, void *x, double tol, const qcd_solve_
  * read once for all right-hand sides) and a second half whose blocks of one
  * site block's right-hand sides run together -- with each right-hand side's
  * own scalars, dot products and exit test; a converged right-hand side is
- * skipped.  Each x_r equals what qcd_solve returns for b_r, bit for bit.
+ * skipped.  (With fewer than 4 right-hand sides the MULT runs per
+ * right-hand side: the staged kernel's tiles would leave the GPU short of
+ * warps.)  Each x_r equals what qcd_solve returns for b_r, bit for bit.
  * b, x: device memory, nrhs canonical full-lattice complex128 vectors back
  * to back ([nrhs][V][4][3]); caller-owned.  infos: NULL or nrhs entries.
  * opts: precision_levels 2, even_odd 1, use_x0 0, outer_df64 0 or 1,
