@@ -7,6 +7,8 @@
 // the solver state in device memory and returns at once when that state is
 // marked done, so a host can queue iterations ahead without reading
 // anything back.
+#include <atomic>
+
 #include "blas.cuh"
 #include "blas_ops.cuh"
 
@@ -30,12 +32,32 @@ __global__ void __launch_bounds__(256) blas_kernel(int n, Op op, RedArgs red, co
     if constexpr (NRED > 0) grid_reduce<NRED>(acc, red);
 }
 
+// Blocks of blas_kernel<NRED, Op> resident on one SM (256 threads each),
+// from the kernel's register and shared-memory needs
+template <int NRED, class Op>
+static int blocks_per_sm()
+{
+    static std::atomic<int> occ{0};
+    int n = occ.load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blas_kernel<NRED, Op>, 256, 0) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = 2;
+        }
+        occ.store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 template <int NRED, class Op>
 static int run(qcd_ctx *c, int nsites, const Op &op, int fin, SolverState *st, const int *done, int cls, double bytes)
 {
     const int threads = 256;
     int blocks = (int)nblocks(nsites, threads);
-    const int cap = 4 * c->num_sms;
+    // one wave of resident blocks walking the sites: a grid larger than the
+    // SMs hold runs its last partial wave at a fraction of the occupancy
+    // (the x, r update at 66 registers holds three blocks per SM, not four)
+    const int cap = blocks_per_sm<NRED, Op>() * c->num_sms;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     RedArgs ra;
