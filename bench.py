@@ -177,6 +177,26 @@ def oracle_dhat_times(dims, U, b, W, reps, openmp):
     return times, threads
 
 
+def oracle_dirac_times(dims, U, b, W, reps, openmp):
+    """Wall times of `reps` oracle D applications (Eq. 3, the full lattice)
+    with the single-threaded build or the OpenMP build on every host core."""
+    import oracle
+
+    threads = oracle.use_openmp(True)
+    F = oracle.clover_field(dims, U, W["kappa"], W["csw"])
+    if not openmp:
+        threads = oracle.use_openmp(False)
+    times = []
+    try:
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            oracle.dirac(dims, W["t_bc"], U, F, W["kappa"], b)
+            times.append(time.perf_counter() - t0)
+    finally:
+        oracle.use_openmp(False)
+    return times, threads
+
+
 def oracle_c1_solve():
     """The oracle's plain FP64 BiCGStab on the 4^4 workload (links exp(i 0.3 H)
     seed 1, kappa 0.12, csw 1.0, source seed 2, tol 1e-12), single-threaded:
@@ -247,13 +267,17 @@ def cpu_baseline_block(dims, U, b, W, n_app):
     t1, _ = oracle_dhat_times(dims, U, b, W, 2, openmp=False)
     tn, threads = oracle_dhat_times(dims, U, b, W, 3, openmp=True)
     d1, dn = min(t1), min(tn)
+    D1, _ = oracle_dirac_times(dims, U, b, W, 1, openmp=False)
+    Dn, _ = oracle_dirac_times(dims, U, b, W, 3, openmp=True)
     n_it, hosts = oracle_iterations()
     return {"value": round(dn * n_app, 3), "unit": "s", "cores": threads, "kind": "oracle",
             "sample": "oracle D^ on the full 24^3x48 lattice, OpenMP build on %d threads (best of 3: %.3f s), "
                       "extrapolated by the %d D^ applications (plus b^_e and x_o) of the FP64 BiCGStab to 1e-12"
                       % (threads, dn, n_app - 2),
-            "single_core": {"dhat_s": round(d1, 3), "solve_s_extrapolated": round(d1 * n_app, 2)},
-            "all_cores": {"threads": threads, "dhat_s": round(dn, 4), "solve_s_extrapolated": round(dn * n_app, 3)},
+            "single_core": {"dhat_s": round(d1, 3), "dirac_s": round(min(D1), 3),
+                            "solve_s_extrapolated": round(d1 * n_app, 2)},
+            "all_cores": {"threads": threads, "dhat_s": round(dn, 4), "dirac_s": round(min(Dn), 4),
+                          "solve_s_extrapolated": round(dn * n_app, 3)},
             "c1_4x4x4x4_full_solve_single_core": oracle_c1_solve(),
             "host": {"nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "oracle_fp64_iterations": n_it, "iterations_by_host": hosts}
@@ -402,6 +426,21 @@ def extra_workloads(torch, qcd, hbm):
                                                                   "ms_per_inner_dhat", "solve_tflops_table1")}
     out["fixed_work_2000_dhat_24x24x24x48"]["what"] = fw["workload"]
     torch.cuda.empty_cache()
+    # ---- the 4^4 workload: plain FP64 BiCGStab on the full D, no preconditioning
+    dims = (4, 4, 4, 4)
+    U = torch.from_numpy(inputs.random_gauge(dims, 0.3, 1)).cuda()
+    b = torch.from_numpy(inputs.gaussian_source(dims, 2)).cuda()
+    c = qcd.Context(dims, -1)
+    c.gauge_load(U)
+    c.clover_build(0.12, 1.0)
+    x = torch.zeros_like(b)
+    t, info = timed_solves(torch, c, b, x, 1e-12, qcd.default_opts(precision_levels=1, even_odd=0, max_outer=5000), 3)
+    out["unpreconditioned_fp64_4x4x4x4"] = {"seconds": round(t, 6), "iterations": info["outer_iters"],
+                                            "true_resid": info["true_resid"],
+                                            "what": "plain FP64 BiCGStab on D (no even-odd), links exp(i 0.3 H) seed 1, "
+                                                    "kappa 0.12, csw 1.0, source seed 2, tol 1e-12"}
+    c.close()
+    del U, b, x
     # ---- adjoint gradient on 16^3x32
     from paper_1709_08785_gb300.autograd import clover_solve
 
