@@ -242,9 +242,10 @@ int qcd_solve(qcd_ctx *ctx, const void *b, void *x, double tol, const qcd_solve_
  * opts: precision_levels 2, even_odd 1, use_x0 0, outer_df64 0 or 1,
  * eo_hermitian 0 (anything else: QCD_EINVAL); 1 <= nrhs <= 16.  The
  * context keeps a workspace of about 16 FP64 and 7 FP32 half vectors per
- * right-hand side until it is destroyed.  Returns QCD_OK when every
- * right-hand side converged, else the first failing status (each entry of
- * infos has its own). */
+ * right-hand side until it is destroyed.  Kernel timing (qcd_set_profiling)
+ * does not bracket the lockstep second halves of D^.  Returns QCD_OK when
+ * every right-hand side converged, else the first failing status (each
+ * entry of infos has its own). */
 int qcd_solve_multi(qcd_ctx *ctx, const void *b, void *x, int nrhs, double tol, const qcd_solve_opts *opts,
                     qcd_solve_info *infos);
 
